@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""SpGEMM benchmark: C = A*B on CSR (int32 indices, float64 values), GFLOP/s and % of HBM roofline.
+
+Workload (one step = the whole pipeline -- binning, symbolic, scan, numeric --
+for both products, inputs resident in HBM, C buffers from torch's caching
+allocator, nnz(C) read back to the host as the C ABI requires):
+  * laplacian5_2048_sq : A = 5-point Laplacian on a 2048 x 2048 grid (4.19M rows), C = A*A
+  * random_1M_k8       : A, B 1M x 1M, 8 distinct uniform columns per row, U(-1,1), C = A*B
+Flops are 2 per multiplication (Section III of the paper).  Inputs total
+~2.5 GB per step, larger than L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain Gustavson of oracle/) on the
+host, on a row sample of the same workload, and prints the same JSON line.
+Under torchrun (N > 1) every rank runs its own replica of the workload (weak
+scaling, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1303_1651_gb300 import roofline, synth  # noqa: E402
+
+METRIC = "SpGEMM GFLOP/s (2/intermediate product) and % HBM roofline; batched vs plain"
+WORKLOAD = "plain_large: laplacian5_2048_sq + random_1M_k8"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "medium"],
+                    help="plain: the benchmark workload; medium: Laplacian 1024^2 + random 500K x 8 "
+                         "(inputs above L2, a few hundred MB; for profiler captures)")
+    ap.add_argument("--verbose", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(kind: str = "plain"):
+    if kind == "medium":
+        L = synth.laplacian5(1024)
+        R1 = synth.random_k(500_000, 8, synth.SEED_A)
+        R2 = synth.random_k(500_000, 8, synth.SEED_B)
+        return [("laplacian5_1024_sq", L, L), ("random_500K_k8", R1, R2)]
+    L = synth.laplacian5(2048)
+    R1 = synth.random_k(1_000_000, 8, synth.SEED_A)
+    R2 = synth.random_k(1_000_000, 8, synth.SEED_B)
+    return [("laplacian5_2048_sq", L, L), ("random_1M_k8", R1, R2)]
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def hbm_peak():
+    p = peaks()
+    if p and p.get("hbm_gbs"):
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("common.cuh", "merge.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1303_1651_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        e = t.get(kernel)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return int(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.lines, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0])); mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle on a row sample of the workload
+# ----------------------------------------------------------------------------------------------
+
+def row_sample(A, frac: float):
+    m = max(1, int(A.rows * frac))
+    nnz = int(A.row_ptr[m])
+    return synth.CSR(m, A.cols, A.row_ptr[:m + 1].copy(), A.col_idx[:nnz].copy(), A.val[:nnz].copy())
+
+
+def oracle_rate(work, frac: float, reps: int = 1):
+    import oracle
+    F = 0
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for _, A, B in work:
+            As = row_sample(A, frac)
+            F += oracle.spgemm(As, B)["F"]
+    dt = time.perf_counter() - t0
+    return 2 * F / dt / 1e9, dt, F
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    work = make_workload(args.workload)
+    frac = 0.25
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_rate(work, frac / 8)
+    t0 = time.perf_counter()
+    F = 0
+    for _ in range(args.steps):
+        _, _, f = oracle_rate(work, frac)
+        F += f
+    dt = time.perf_counter() - t0
+    value = 2 * F / dt / 1e9
+    sample = f"first {int(frac * 100)}% of the rows of A in each product, full B, per step"
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": sample, "indices": "int32 (oracle uses int64)"},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1303_1651_gb300 import binding, build
+    build.build()
+    binding.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    work = make_workload(args.workload)
+    stream = torch.cuda.current_stream()
+    prods = []
+    for name, A, B in work:
+        dA = binding.DeviceCSR.from_host(A, dev)
+        dB = dA if B is A else binding.DeviceCSR.from_host(B, dev)
+        ws = torch.empty(binding.spgemm_workspace_size(dA, dB), dtype=torch.uint8, device=dev)
+        C_rp = torch.empty(A.rows + 1, dtype=torch.int32, device=dev)
+        prods.append(dict(name=name, A=A, B=B, dA=dA, dB=dB, ws=ws, C_rp=C_rp,
+                          ev0=[], ev1=[]))
+
+    def one_product(p, record: bool):
+        plan = binding.spgemm_plan(p["dA"], p["dB"], p["ws"], None, stream)
+        try:
+            nnz = binding.spgemm_symbolic(plan, p["C_rp"], stream)
+            C_col = torch.empty(nnz, dtype=torch.int32, device=dev)
+            C_val = torch.empty(nnz, dtype=torch.float64, device=dev)
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            binding.spgemm_numeric(plan, p["dA"].val, p["dB"].val, C_col, C_val, stream)
+            if record:
+                e1.record(stream)
+                p["ev0"].append(e0); p["ev1"].append(e1)
+            p["info"] = binding.spgemm_plan_info(plan)
+            p["nnz"] = nnz
+        finally:
+            binding.spgemm_free(plan)
+        return C_col, C_val
+
+    def step(record=False):
+        for p in prods:
+            one_product(p, record)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(record=True)
+        t1.record(stream)
+        barrier()
+    ms = t0.elapsed_time(t1) / args.steps
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    F_total = sum(p["info"]["products"] for p in prods)
+    flop_step = 2 * F_total
+    value = world * flop_step / (ms * 1e-3) / 1e9
+    bw, bw_kind = hbm_peak()
+    detail = {}
+    bytes_step = 0
+    dominant = None
+    for p in prods:
+        bmin = roofline.bytes_min(p["A"], p["B"], p["nnz"])
+        bytes_step += bmin
+        num_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(p["ev0"], p["ev1"])]))
+        cls = p["info"]["rows_per_class"]
+        kern = "k_merge<numeric," + ("1024" if cls["M1"] >= cls["M2"] else "2048") + ">"
+        d = {"F": p["info"]["products"], "nnz_c": p["nnz"], "bytes_min": bmin, "numeric_ms": num_ms,
+             "numeric_kernel": kern, "rows_per_class": cls,
+             "numeric_gbs": bmin / (num_ms * 1e-3) / 1e9}
+        detail[p["name"]] = d
+        if dominant is None or num_ms > detail[dominant]["numeric_ms"]:
+            dominant = p["name"]
+    dom = detail[dominant]
+    achieved = dom["numeric_gbs"]
+    roof = {"bound": "hbm", "achieved": achieved, "peak": bw, "unit": "GB/s", "frac": achieved / bw,
+            "traffic": committed_traffic(dom["numeric_kernel"]), "kernel": dom["numeric_kernel"],
+            "workload": dominant, "peak_kind": f"{bw_kind} (MEASURED_PEAKS.json hbm_gbs)",
+            "step_frac_of_hbm_roofline": bytes_step / (ms * 1e-3) / 1e9 / bw,
+            "algorithmic_bytes": "read A (4(m+1)+12nnzA) + each referenced B row once + write C (4(m+1)+12nnzC)"}
+    launches_per_step = 0
+    for p in prods:
+        nonempty = sum(1 for v in p["info"]["rows_per_class"].values() if v > 0)
+        launches_per_step += 1 + nonempty + 1 + nonempty   # bin, symbolic per class, scan, numeric per class
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = run_e2e(args, prods, dev, stream, binding, torch, world)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        rate, dt, F = oracle_rate(work, 1.0 / 16)
+        cpu = {"value": rate, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"first 1/16 of the rows of A in each product, full B ({dt:.1f} s, {F} products)"}
+
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.workload == "plain" else args.workload, "indices": "int32", "values": "float64",
+                       "l2": "inputs (~2.5 GB per step) larger than L2; no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(), "detail": detail}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, prods, dev, stream, binding, torch, world):
+    """Same metric through the C ABI with host buffers: H2D of A, B and D2H of C inside the timed region."""
+    host = []
+    h2d = d2h = 0
+    for p in prods:
+        A, B = p["A"], p["B"]
+        hA = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (A.row_ptr, A.col_idx, A.val)]
+        hB = hA if B is A else [torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+                                for x in (B.row_ptr, B.col_idx, B.val)]
+        dA = binding.DeviceCSR(A.rows, A.cols, *[torch.empty_like(t, device=dev) for t in hA])
+        dB = dA if B is A else binding.DeviceCSR(B.rows, B.cols, *[torch.empty_like(t, device=dev) for t in hB])
+        nnz = p["nnz"]
+        outs = [torch.empty(A.rows + 1, dtype=torch.int32).pin_memory(),
+                torch.empty(nnz, dtype=torch.int32).pin_memory(), torch.empty(nnz, dtype=torch.float64).pin_memory()]
+        host.append((p, hA, hB, dA, dB, outs))
+        h2d += sum(t.numel() * t.element_size() for t in hA)
+        if B is not A:
+            h2d += sum(t.numel() * t.element_size() for t in hB)
+        d2h += sum(t.numel() * t.element_size() for t in outs)
+
+    def e2e_step():
+        for p, hA, hB, dA, dB, outs in host:
+            for d, h in zip((dA.row_ptr, dA.col_idx, dA.val), hA):
+                d.copy_(h, non_blocking=True)
+            if dB is not dA:
+                for d, h in zip((dB.row_ptr, dB.col_idx, dB.val), hB):
+                    d.copy_(h, non_blocking=True)
+            plan = binding.spgemm_plan(dA, dB, p["ws"], None, stream)
+            try:
+                nnz = binding.spgemm_symbolic(plan, p["C_rp"], stream)
+                C_col = torch.empty(nnz, dtype=torch.int32, device=dev)
+                C_val = torch.empty(nnz, dtype=torch.float64, device=dev)
+                binding.spgemm_numeric(plan, dA.val, dB.val, C_col, C_val, stream)
+                outs[0].copy_(p["C_rp"], non_blocking=True)
+                outs[1].copy_(C_col, non_blocking=True)
+                outs[2].copy_(C_val, non_blocking=True)
+            finally:
+                binding.spgemm_free(plan)
+        torch.cuda.synchronize()
+
+    steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e2e_step()
+    dt = (time.perf_counter() - t0) / steps
+    F_total = sum(p["info"]["products"] for p in prods)
+    return {"value": world * 2 * F_total / dt / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": steps}
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

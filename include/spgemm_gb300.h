@@ -1,0 +1,172 @@
+/*
+ * spgemm_gb300.h -- C ABI of the GB300 sparse x sparse product C = A * B.
+ *
+ * The operation is the sparse matrix-matrix multiplication (spMMM) analysed in
+ * Scharpff, Iglberger, Hager, Ruede, "Model-guided Performance Analysis of the
+ * Sparse Matrix-Matrix Multiplication" (arXiv:1303.1651):
+ *   - Section IV-A: the row-major (Gustavson) algorithm on three CSR matrices --
+ *     row r of C is the sum over the entries a_rj of row r of A of a_rj times
+ *     row j of B;
+ *   - Section IV-B: the result is stored row by row, columns ascending within a
+ *     row, into one contiguous block sized once from a never-underestimating nnz
+ *     estimate (the number of multiplications);
+ *   - Section III: the multiplication count sum_k nnz(A(:,k)) * nnz(B(k,:)) and
+ *     the flop convention of two flops per multiplication.
+ *
+ * Matrices are CSR with int32 row pointers and column indices and float64
+ * values (the paper stores 64-bit indices; this library uses 32-bit ones and
+ * reports SPGEMM_ERR_OVERFLOW where a count does not fit).
+ *
+ * Semantics:
+ *   - The structure of C is the union of the structures of the scaled rows of
+ *     B: an entry whose products cancel to 0.0, or that comes from an explicit
+ *     zero in A or B, is stored.
+ *   - Rows of C come out sorted by column, without duplicates.
+ *   - Rows of A may be in any order and may repeat a column.  Rows of B must be
+ *     sorted by column for the merge classes (rows of up to 8 entries of A and
+ *     64 products); when they are not, spgemm_symbolic returns
+ *     SPGEMM_ERR_UNSORTED.
+ *   - Each value of C is a sum of products a_rj * b_jx rounded one by one
+ *     (no fused multiply-add).
+ *
+ * Memory and ownership:
+ *   - All matrix arrays and the workspace are DEVICE pointers owned by the
+ *     caller, who must keep them alive and unchanged until the last call that
+ *     uses them has completed on its stream.
+ *   - The library allocates no device memory.  spgemm_plan allocates the small
+ *     host-side plan object, which spgemm_free releases.
+ *   - A plan is not thread-safe.  Use it from one host thread and on one stream
+ *     at a time.
+ *
+ * Streams: every call enqueues its work on `stream` (a cudaStream_t; NULL is the
+ * legacy default stream).  spgemm_plan and spgemm_symbolic synchronise `stream`
+ * before they return, to read back the row classes and nnz(C); spgemm_numeric
+ * does not.
+ *
+ * Errors: every function returns an spgemm_status_t.  Device-side errors
+ * (table overflow, a changed pattern, a bounded wait that gave up) are sticky
+ * in the plan and are reported by the next synchronising call, or by
+ * spgemm_status.  No kernel traps or waits without a bound.
+ */
+#ifndef SPGEMM_GB300_H
+#define SPGEMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPGEMM_OK = 0,
+  SPGEMM_ERR_INVALID = 1,     /* bad argument: NULL pointer, negative size, A.cols != B.rows,
+                                 a column index out of range, a decreasing row pointer */
+  SPGEMM_ERR_ALLOC = 2,       /* the workspace passed is smaller than spgemm_workspace_size */
+  SPGEMM_ERR_OVERFLOW = 3,    /* nnz(C), or the products of one row, exceed INT32_MAX */
+  SPGEMM_ERR_TABLE_FULL = 4,  /* a hash table ran out of slots (cannot happen within the class limits) */
+  SPGEMM_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed */
+  SPGEMM_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+  SPGEMM_ERR_STATE = 7,       /* calls made out of order (numeric before symbolic, ...) */
+  SPGEMM_ERR_UNSORTED = 8,    /* a row of B used by a merge-class row is not sorted by column */
+  SPGEMM_ERR_MISMATCH = 9     /* numeric found a different structure than symbolic (inputs changed) */
+} spgemm_status_t;
+
+/* A CSR matrix in device memory.  row_ptr has rows+1 entries with row_ptr[0] = 0 and
+ * row_ptr[rows] = nnz; col_idx and val have nnz entries.  val may be NULL where only the
+ * structure is read (spgemm_plan, spgemm_symbolic). */
+typedef struct {
+  int32_t rows;
+  int32_t cols;
+  int64_t nnz;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+} spgemm_csr_t;
+
+/* Tuning knobs.  A zero field takes the default.  Limits larger than what a class's kernel
+ * can hold are clamped to it.  Row classes are chosen per row from k_r (the number of
+ * entries of row r of A) and u_r (its multiplications), in the spirit of the per-row
+ * strategy switch of the "Combined" kernel (Section IV-B). */
+typedef struct {
+  int32_t merge_max_k;    /* rows with k_r <= this (max 8) may use the merge classes (default 8) */
+  int32_t m1_max_u;       /* merge class M1 (1024-product warp tiles): u_r <= this (max 32, default 32) */
+  int32_t m2_max_u;       /* merge class M2 (2048-product warp tiles): u_r <= this (max 64, default 64) */
+  int32_t warp_max_u;     /* warp-per-row hash class W: u_r <= this (max 512, default 512) */
+  int32_t block_max_u;    /* block-per-row hash class B: u_r <= this (max 4096, default 4096);
+                             longer rows use a dense accumulator in global memory (class G) */
+  int32_t dense_slabs;    /* CTAs (each owning one dense accumulator of B.cols doubles) for class G
+                             (default 2) */
+  int32_t validate;       /* nonzero: also check row_ptr monotonicity and every column index of A and
+                             B before planning (one extra pass over both matrices) */
+  int32_t reserved[9];
+} spgemm_options_t;
+
+/* Counters of a plan, valid after spgemm_plan (and nnz_c after spgemm_symbolic). */
+typedef struct {
+  int64_t products;       /* F = sum_r u_r: multiplications (Section III); flops = 2 F */
+  int64_t nnz_c;          /* nnz(C), -1 before spgemm_symbolic */
+  int32_t max_row_products;
+  int32_t rows_per_class[5];   /* M1, M2, W, B, G */
+} spgemm_info_t;
+
+typedef struct spgemm_plan_s* spgemm_plan_t;
+
+/* Bytes of device workspace that spgemm_plan needs for this A (rows) and B (cols).  It depends
+ * only on the shapes and the options, not on the device data.  Returns SPGEMM_ERR_INVALID for
+ * negative sizes or mismatched inner dimensions. */
+spgemm_status_t spgemm_workspace_size(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
+                                      size_t* bytes);
+
+/* Plan C = A * B: a1 of the pipeline -- per-row multiplication counts u_r, the row classes
+ * and per-class row lists, and F (Section III count; the Section IV-B nnz estimate).
+ *   out        -- receives the new plan (host object; release it with spgemm_free).
+ *   A, B       -- device CSR descriptors; only the structure is read here.  The descriptors are
+ *                 copied; the arrays they point to must stay valid for the plan's lifetime.
+ *   opt        -- may be NULL (defaults).
+ *   workspace  -- device memory of at least workspace_bytes >= spgemm_workspace_size(...),
+ *                 256-byte aligned, owned by the caller, used exclusively by this plan.
+ * Enqueues on stream and synchronises it.  Errors: INVALID, ALLOC, OVERFLOW, CUDA. */
+spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spgemm_csr_t* B,
+                            const spgemm_options_t* opt, void* workspace, size_t workspace_bytes,
+                            void* stream);
+
+/* a2 + a3: count the distinct columns of every row of C and build C's row pointer.
+ *   C_row_ptr -- device, A.rows + 1 int32, written with the exclusive prefix sums
+ *                (C_row_ptr[0] = 0, C_row_ptr[rows] = nnz(C)).
+ *   nnz_c     -- host, receives nnz(C) (size C_col/C_val with it).
+ * Enqueues on stream and synchronises it.  Errors: STATE, OVERFLOW (nnz(C) > INT32_MAX),
+ * UNSORTED, TABLE_FULL, TIMEOUT, CUDA.  May be called again (re-runs the symbolic pass). */
+spgemm_status_t spgemm_symbolic(spgemm_plan_t plan, int32_t* C_row_ptr, int64_t* nnz_c, void* stream);
+
+/* a4: compute C's column indices and values.
+ *   A_val, B_val -- device values aligned with A's and B's entries (may differ between calls;
+ *                   the structure must be the one planned).
+ *   C_col, C_val -- device, nnz(C) entries each.  The C_row_ptr given to spgemm_symbolic must
+ *                   still hold its result.
+ * Enqueues on stream and returns without synchronising; repeatable.  Errors: STATE, INVALID
+ * (NULL value pointers), CUDA.  A structure that changed since spgemm_symbolic is reported
+ * as SPGEMM_ERR_MISMATCH by spgemm_status. */
+spgemm_status_t spgemm_numeric(spgemm_plan_t plan, const double* A_val, const double* B_val, int32_t* C_col,
+                               double* C_val, void* stream);
+
+/* Synchronise stream and report the plan's sticky device status (OK or the first error). */
+spgemm_status_t spgemm_status(spgemm_plan_t plan, void* stream);
+
+/* Copy the plan's counters (host-side copies; no synchronisation). */
+spgemm_status_t spgemm_plan_info(spgemm_plan_t plan, spgemm_info_t* info);
+
+/* Release the plan object.  The workspace stays the caller's.  NULL is accepted. */
+spgemm_status_t spgemm_free(spgemm_plan_t plan);
+
+/* Static string naming a status code. */
+const char* spgemm_error_string(int code);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int32_t spgemm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPGEMM_GB300_H */

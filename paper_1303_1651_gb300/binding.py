@@ -1,0 +1,245 @@
+"""ctypes binding of the C ABI in include/spgemm_gb300.h (argument marshalling only).
+
+Every step of the product runs in the CUDA library; this module turns torch
+tensors into device pointers and sizes, passes the current CUDA stream, and
+raises ``SpgemmError`` on a non-zero status.  If the library has not been
+built, ``load()`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lib = None
+
+SPGEMM_STATUS = {
+    0: "SPGEMM_OK", 1: "SPGEMM_ERR_INVALID", 2: "SPGEMM_ERR_ALLOC", 3: "SPGEMM_ERR_OVERFLOW",
+    4: "SPGEMM_ERR_TABLE_FULL", 5: "SPGEMM_ERR_CUDA", 6: "SPGEMM_ERR_TIMEOUT", 7: "SPGEMM_ERR_STATE",
+    8: "SPGEMM_ERR_UNSORTED", 9: "SPGEMM_ERR_MISMATCH",
+}
+CLASS_NAMES = ("M1", "M2", "W", "B", "G")
+
+
+class SpgemmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        self.name = SPGEMM_STATUS.get(code, str(code))
+        super().__init__(f"{where}: {self.name} ({error_string(code) if _lib else code})")
+
+
+class spgemm_csr_t(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class spgemm_options_t(ctypes.Structure):
+    _fields_ = [("merge_max_k", ctypes.c_int32), ("m1_max_u", ctypes.c_int32), ("m2_max_u", ctypes.c_int32),
+                ("warp_max_u", ctypes.c_int32), ("block_max_u", ctypes.c_int32), ("dense_slabs", ctypes.c_int32),
+                ("validate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+
+
+class spgemm_info_t(ctypes.Structure):
+    _fields_ = [("products", ctypes.c_int64), ("nnz_c", ctypes.c_int64), ("max_row_products", ctypes.c_int32),
+                ("rows_per_class", ctypes.c_int32 * 5)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the CUDA library (built in-tree); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"SpGEMM CUDA library not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        vp = ctypes.c_void_p
+        lib.spgemm_workspace_size.argtypes = [P(spgemm_csr_t), P(spgemm_csr_t), P(spgemm_options_t),
+                                              P(ctypes.c_size_t)]
+        lib.spgemm_plan.argtypes = [P(vp), P(spgemm_csr_t), P(spgemm_csr_t), P(spgemm_options_t), vp,
+                                    ctypes.c_size_t, vp]
+        lib.spgemm_symbolic.argtypes = [vp, vp, P(ctypes.c_int64), vp]
+        lib.spgemm_numeric.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.spgemm_status.argtypes = [vp, vp]
+        lib.spgemm_plan_info.argtypes = [vp, P(spgemm_info_t)]
+        lib.spgemm_free.argtypes = [vp]
+        lib.spgemm_error_string.argtypes = [ctypes.c_int]
+        lib.spgemm_error_string.restype = ctypes.c_char_p
+        lib.spgemm_version.restype = ctypes.c_int32
+        for name in ("spgemm_workspace_size", "spgemm_plan", "spgemm_symbolic", "spgemm_numeric",
+                     "spgemm_status", "spgemm_plan_info", "spgemm_free"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return load().spgemm_error_string(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise SpgemmError(code, where)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None or t.numel() == 0:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+@dataclass
+class DeviceCSR:
+    """CSR matrix in device memory: int32 row_ptr/col_idx, float64 val (torch tensors)."""
+
+    rows: int
+    cols: int
+    row_ptr: torch.Tensor
+    col_idx: torch.Tensor
+    val: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_idx.numel())
+
+    @staticmethod
+    def from_host(M, device="cuda") -> "DeviceCSR":
+        return DeviceCSR(M.rows, M.cols,
+                         torch.from_numpy(np.ascontiguousarray(M.row_ptr, np.int32)).to(device),
+                         torch.from_numpy(np.ascontiguousarray(M.col_idx, np.int32)).to(device),
+                         torch.from_numpy(np.ascontiguousarray(M.val, np.float64)).to(device))
+
+    def desc(self, with_values: bool = True) -> spgemm_csr_t:
+        return spgemm_csr_t(self.rows, self.cols, self.nnz, _ptr(self.row_ptr), _ptr(self.col_idx),
+                            _ptr(self.val) if with_values else None)
+
+    def to_host(self) -> dict:
+        return dict(rows=self.rows, cols=self.cols, row_ptr=self.row_ptr.cpu().numpy(),
+                    col_idx=self.col_idx.cpu().numpy(), val=self.val.cpu().numpy(), nnz=self.nnz)
+
+
+def options(**kw) -> spgemm_options_t:
+    o = spgemm_options_t()
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+# ---- thin wrappers with the C names --------------------------------------------------------
+
+def spgemm_workspace_size(A: DeviceCSR, B: DeviceCSR, opt: spgemm_options_t | None = None) -> int:
+    n = ctypes.c_size_t(0)
+    a, b = A.desc(False), B.desc(False)
+    _check(load().spgemm_workspace_size(ctypes.byref(a), ctypes.byref(b), ctypes.byref(opt) if opt else None,
+                                        ctypes.byref(n)), "spgemm_workspace_size")
+    return int(n.value)
+
+
+def spgemm_plan(A: DeviceCSR, B: DeviceCSR, workspace: torch.Tensor, opt: spgemm_options_t | None = None,
+                stream=None) -> int:
+    h = ctypes.c_void_p(0)
+    a, b = A.desc(False), B.desc(False)
+    _check(load().spgemm_plan(ctypes.byref(h), ctypes.byref(a), ctypes.byref(b),
+                              ctypes.byref(opt) if opt else None, workspace.data_ptr(),
+                              workspace.numel() * workspace.element_size(), _stream(stream)), "spgemm_plan")
+    return h.value
+
+
+def spgemm_symbolic(plan: int, C_row_ptr: torch.Tensor, stream=None) -> int:
+    nnz = ctypes.c_int64(0)
+    _check(load().spgemm_symbolic(plan, C_row_ptr.data_ptr(), ctypes.byref(nnz), _stream(stream)),
+           "spgemm_symbolic")
+    return int(nnz.value)
+
+
+def spgemm_numeric(plan: int, A_val: torch.Tensor, B_val: torch.Tensor, C_col: torch.Tensor, C_val: torch.Tensor,
+                   stream=None):
+    _check(load().spgemm_numeric(plan, _ptr(A_val), _ptr(B_val), _ptr(C_col), _ptr(C_val), _stream(stream)),
+           "spgemm_numeric")
+
+
+def spgemm_status(plan: int, stream=None):
+    _check(load().spgemm_status(plan, _stream(stream)), "spgemm_status")
+
+
+def spgemm_plan_info(plan: int) -> dict:
+    info = spgemm_info_t()
+    _check(load().spgemm_plan_info(plan, ctypes.byref(info)), "spgemm_plan_info")
+    return dict(products=int(info.products), nnz_c=int(info.nnz_c), max_row_products=int(info.max_row_products),
+                rows_per_class=dict(zip(CLASS_NAMES, list(info.rows_per_class))))
+
+
+def spgemm_free(plan: int):
+    if plan:
+        load().spgemm_free(plan)
+
+
+# ---- the whole product ----------------------------------------------------------------------
+
+class Product:
+    """One planned product C = A*B: workspace, plan, C's row pointer; numeric is repeatable."""
+
+    def __init__(self, A: DeviceCSR, B: DeviceCSR, opt: spgemm_options_t | None = None, stream=None,
+                 workspace: torch.Tensor | None = None):
+        if A.cols != B.rows:
+            raise ValueError("inner dimensions differ")
+        self.A, self.B, self.opt = A, B, opt
+        dev = A.row_ptr.device
+        need = spgemm_workspace_size(A, B, opt)
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+        self.workspace = workspace
+        self.plan = spgemm_plan(A, B, workspace, opt, stream)
+        self.C_row_ptr = torch.empty(A.rows + 1, dtype=torch.int32, device=dev)
+        self.nnz = spgemm_symbolic(self.plan, self.C_row_ptr, stream)
+        self.info = spgemm_plan_info(self.plan)
+
+    def numeric(self, A_val=None, B_val=None, C_col=None, C_val=None, stream=None) -> DeviceCSR:
+        dev = self.A.row_ptr.device
+        A_val = self.A.val if A_val is None else A_val
+        B_val = self.B.val if B_val is None else B_val
+        if C_col is None:
+            C_col = torch.empty(self.nnz, dtype=torch.int32, device=dev)
+        if C_val is None:
+            C_val = torch.empty(self.nnz, dtype=torch.float64, device=dev)
+        spgemm_numeric(self.plan, A_val, B_val, C_col, C_val, stream)
+        return DeviceCSR(self.A.rows, self.B.cols, self.C_row_ptr, C_col, C_val)
+
+    def close(self):
+        if getattr(self, "plan", None):
+            spgemm_free(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def multiply(A: DeviceCSR, B: DeviceCSR, opt: spgemm_options_t | None = None, stream=None,
+             check: bool = False) -> DeviceCSR:
+    """C = A*B on the GPU through plan / symbolic / numeric."""
+    prod = Product(A, B, opt, stream)
+    try:
+        C = prod.numeric(stream=stream)
+        if check:
+            spgemm_status(prod.plan, stream)
+        return C
+    finally:
+        prod.close()

@@ -1,0 +1,38 @@
+// Host-side launchers between the C-ABI layer (api.cu) and the kernel files.
+#pragma once
+#include <cstddef>
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace spg {
+
+// a1: per-row product counts, row classes, class lists, F, max row count (binning).
+void launch_bin(const DevCsr& A, const DevCsr& B, const Limits& lim, uint8_t* cls, int* const lists[NUM_CLS],
+                Counters* ctr, cudaStream_t s);
+
+// a3: exclusive scan, in place, of counts[0..n-2] into row_ptr[0..n-1] (n = rows + 1).
+size_t scan_tile_state_bytes(long long n);
+void launch_scan(int* rp, long long n, unsigned long long* tile_state, Counters* ctr, cudaStream_t s);
+
+// a2/a4, merge classes: warp tiles of 32 consecutive rows, rows of class `cls` only.
+void launch_merge_symbolic(int cls, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* counts,
+                           Counters* ctr, cudaStream_t s);
+void launch_merge_numeric(int cls, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, const int* rp,
+                          int* C_col, double* C_val, Counters* ctr, cudaStream_t s);
+
+// a2/a4, hash classes W (warp per row) and B (block per row), rows from a list.
+void launch_hash_symbolic(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts,
+                          Counters* ctr, cudaStream_t s);
+void launch_hash_numeric(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, const int* rp,
+                         int* C_col, double* C_val, Counters* ctr, cudaStream_t s);
+
+// a2/a4, class G: dense accumulator slabs in global memory (one slab per CTA).
+size_t dense_slab_bytes(int ncols);
+void launch_dense_symbolic(const DevCsr& A, const DevCsr& B, const int* list, int count, void* slabs, int nslabs,
+                           int* counts, Counters* ctr, cudaStream_t s);
+void launch_dense_numeric(const DevCsr& A, const DevCsr& B, const int* list, int count, void* slabs, int nslabs,
+                          const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace spg
