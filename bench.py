@@ -225,23 +225,34 @@ def run_ours(args, rank, world, local_rank):
                           ev0=[], ev1=[]))
 
     def one_product(p, record: bool):
+        """plan (binning, F read back) -> C sized by F -> single-pass compute (nnz(C) read back)."""
+        plan = binding.spgemm_plan(p["dA"], p["dB"], p["ws"], None, stream)
+        try:
+            info = binding.spgemm_plan_info(plan)
+            F = info["products"]
+            C_col = torch.empty(max(F, 1), dtype=torch.int32, device=dev)
+            C_val = torch.empty(max(F, 1), dtype=torch.float64, device=dev)
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                binding.spgemm_plan_set_events(plan, e0, e1)
+                p["ev0"].append(e0); p["ev1"].append(e1)
+            nnz = binding.spgemm_compute(plan, p["dA"].val, p["dB"].val, p["C_rp"], C_col, C_val, stream)
+            p["info"] = info
+            p["nnz"] = nnz
+        finally:
+            binding.spgemm_free(plan)
+        return C_col, C_val
+
+    def one_product_3call(p):
+        """plan -> symbolic (row pointer, nnz(C) read back) -> numeric."""
         plan = binding.spgemm_plan(p["dA"], p["dB"], p["ws"], None, stream)
         try:
             nnz = binding.spgemm_symbolic(plan, p["C_rp"], stream)
             C_col = torch.empty(nnz, dtype=torch.int32, device=dev)
             C_val = torch.empty(nnz, dtype=torch.float64, device=dev)
-            if record:
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
             binding.spgemm_numeric(plan, p["dA"].val, p["dB"].val, C_col, C_val, stream)
-            if record:
-                e1.record(stream)
-                p["ev0"].append(e0); p["ev1"].append(e1)
-            p["info"] = binding.spgemm_plan_info(plan)
-            p["nnz"] = nnz
         finally:
             binding.spgemm_free(plan)
-        return C_col, C_val
 
     def step(record=False):
         for p in prods:
@@ -250,6 +261,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
+
     def barrier():
         if dist:
             dist.barrier()
@@ -270,6 +282,20 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
 
+    # the three-call path (plan / symbolic / numeric) on the same inputs, for comparison
+    for _ in range(2):
+        for p in prods:
+            one_product_3call(p)
+    torch.cuda.synchronize()
+    a3, b3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a3.record(stream)
+    for _ in range(args.steps):
+        for p in prods:
+            one_product_3call(p)
+    b3.record(stream)
+    torch.cuda.synchronize()
+    ms_3call = a3.elapsed_time(b3) / args.steps
+
     F_total = sum(p["info"]["products"] for p in prods)
     flop_step = 2 * F_total
     value = world * flop_step / (ms * 1e-3) / 1e9
@@ -282,24 +308,27 @@ def run_ours(args, rank, world, local_rank):
         bytes_step += bmin
         num_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(p["ev0"], p["ev1"])]))
         cls = p["info"]["rows_per_class"]
-        kern = "k_merge<numeric," + ("1024" if cls["M1"] >= cls["M2"] else "2048") + ">"
-        d = {"F": p["info"]["products"], "nnz_c": p["nnz"], "bytes_min": bmin, "numeric_ms": num_ms,
-             "numeric_kernel": kern, "rows_per_class": cls,
-             "numeric_gbs": bmin / (num_ms * 1e-3) / 1e9}
+        wide = p["info"]["max_row_products"] > 32 and cls["M2"] > 0
+        kern = "k_merge<fused," + ("64" if wide else "32") + ">"
+        d = {"F": p["info"]["products"], "nnz_c": p["nnz"], "bytes_min": bmin, "compute_ms": num_ms,
+             "compute_kernel": kern, "rows_per_class": cls,
+             "compute_gbs": bmin / (num_ms * 1e-3) / 1e9,
+             "compute_gflops": 2 * p["info"]["products"] / (num_ms * 1e-3) / 1e9}
         detail[p["name"]] = d
-        if dominant is None or num_ms > detail[dominant]["numeric_ms"]:
+        if dominant is None or num_ms > detail[dominant]["compute_ms"]:
             dominant = p["name"]
     dom = detail[dominant]
-    achieved = dom["numeric_gbs"]
+    achieved = dom["compute_gbs"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": bw, "unit": "GB/s", "frac": achieved / bw,
-            "traffic": committed_traffic(dom["numeric_kernel"]), "kernel": dom["numeric_kernel"],
+            "traffic": committed_traffic(dom["compute_kernel"]), "kernel": dom["compute_kernel"],
             "workload": dominant, "peak_kind": f"{bw_kind} (MEASURED_PEAKS.json hbm_gbs)",
             "step_frac_of_hbm_roofline": bytes_step / (ms * 1e-3) / 1e9 / bw,
             "algorithmic_bytes": "read A (4(m+1)+12nnzA) + each referenced B row once + write C (4(m+1)+12nnzC)"}
     launches_per_step = 0
     for p in prods:
-        nonempty = sum(1 for v in p["info"]["rows_per_class"].values() if v > 0)
-        launches_per_step += 1 + nonempty + 1 + nonempty   # bin, symbolic per class, scan, numeric per class
+        cls = p["info"]["rows_per_class"]
+        others = sum(1 for c in ("W", "B", "G") if cls[c] > 0)
+        launches_per_step += 1 + 1 + 2 * others   # bin, fused merge pass, symbolic + numeric per other class
 
     # end to end through the C ABI from pinned host buffers
     e2e = run_e2e(args, prods, dev, stream, binding, torch, world)
@@ -318,7 +347,10 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
-            "clocks": clk.summary(), "detail": detail}
+            "clocks": clk.summary(), "detail": detail,
+            "three_call": {"ms_per_step": ms_3call, "value": world * flop_step / (ms_3call * 1e-3) / 1e9,
+                           "path": "plan / symbolic / numeric"},
+            "path": "plan (binning, F read back) + single-pass compute (nnz(C) read back)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -354,13 +386,13 @@ def run_e2e(args, prods, dev, stream, binding, torch, world):
                     d.copy_(h, non_blocking=True)
             plan = binding.spgemm_plan(dA, dB, p["ws"], None, stream)
             try:
-                nnz = binding.spgemm_symbolic(plan, p["C_rp"], stream)
-                C_col = torch.empty(nnz, dtype=torch.int32, device=dev)
-                C_val = torch.empty(nnz, dtype=torch.float64, device=dev)
-                binding.spgemm_numeric(plan, dA.val, dB.val, C_col, C_val, stream)
+                F = binding.spgemm_plan_info(plan)["products"]
+                C_col = torch.empty(max(F, 1), dtype=torch.int32, device=dev)
+                C_val = torch.empty(max(F, 1), dtype=torch.float64, device=dev)
+                nnz = binding.spgemm_compute(plan, dA.val, dB.val, p["C_rp"], C_col, C_val, stream)
                 outs[0].copy_(p["C_rp"], non_blocking=True)
-                outs[1].copy_(C_col, non_blocking=True)
-                outs[2].copy_(C_val, non_blocking=True)
+                outs[1].copy_(C_col[:nnz], non_blocking=True)
+                outs[2].copy_(C_val[:nnz], non_blocking=True)
             finally:
                 binding.spgemm_free(plan)
         torch.cuda.synchronize()

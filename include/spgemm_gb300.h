@@ -22,10 +22,8 @@
  *     B: an entry whose products cancel to 0.0, or that comes from an explicit
  *     zero in A or B, is stored.
  *   - Rows of C come out sorted by column, without duplicates.
- *   - Rows of A may be in any order and may repeat a column.  Rows of B must be
- *     sorted by column for the merge classes (rows of up to 8 entries of A and
- *     64 products); when they are not, spgemm_symbolic returns
- *     SPGEMM_ERR_UNSORTED.
+ *   - Rows of A and of B may be in any order and may repeat a column (repeated
+ *     entries each contribute their products).
  *   - Each value of C is a sum of products a_rj * b_jx rounded one by one
  *     (no fused multiply-add).
  *
@@ -68,7 +66,7 @@ typedef enum {
   SPGEMM_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed */
   SPGEMM_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
   SPGEMM_ERR_STATE = 7,       /* calls made out of order (numeric before symbolic, ...) */
-  SPGEMM_ERR_UNSORTED = 8,    /* a row of B used by a merge-class row is not sorted by column */
+  SPGEMM_ERR_UNSORTED = 8,    /* reserved (inputs need not be sorted; not returned by this version) */
   SPGEMM_ERR_MISMATCH = 9     /* numeric found a different structure than symbolic (inputs changed) */
 } spgemm_status_t;
 
@@ -90,8 +88,8 @@ typedef struct {
  * strategy switch of the "Combined" kernel (Section IV-B). */
 typedef struct {
   int32_t merge_max_k;    /* rows with k_r <= this (max 8) may use the merge classes (default 8) */
-  int32_t m1_max_u;       /* merge class M1 (1024-product warp tiles): u_r <= this (max 32, default 32) */
-  int32_t m2_max_u;       /* merge class M2 (2048-product warp tiles): u_r <= this (max 64, default 64) */
+  int32_t m1_max_u;       /* class M1 (thread-per-row sort of <= 32 products): u_r <= this (max 32, default 32) */
+  int32_t m2_max_u;       /* class M2 (thread-per-row sort of <= 64 products): u_r <= this (max 64, default 64) */
   int32_t warp_max_u;     /* warp-per-row hash class W: u_r <= this (max 512, default 512) */
   int32_t block_max_u;    /* block-per-row hash class B: u_r <= this (max 4096, default 4096);
                              longer rows use a dense accumulator in global memory (class G) */
@@ -136,7 +134,7 @@ spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spg
  *                (C_row_ptr[0] = 0, C_row_ptr[rows] = nnz(C)).
  *   nnz_c     -- host, receives nnz(C) (size C_col/C_val with it).
  * Enqueues on stream and synchronises it.  Errors: STATE, OVERFLOW (nnz(C) > INT32_MAX),
- * UNSORTED, TABLE_FULL, TIMEOUT, CUDA.  May be called again (re-runs the symbolic pass). */
+ * TABLE_FULL, TIMEOUT, CUDA.  May be called again (re-runs the symbolic pass). */
 spgemm_status_t spgemm_symbolic(spgemm_plan_t plan, int32_t* C_row_ptr, int64_t* nnz_c, void* stream);
 
 /* a4: compute C's column indices and values.
@@ -150,11 +148,31 @@ spgemm_status_t spgemm_symbolic(spgemm_plan_t plan, int32_t* C_row_ptr, int64_t*
 spgemm_status_t spgemm_numeric(spgemm_plan_t plan, const double* A_val, const double* B_val, int32_t* C_col,
                                double* C_val, void* stream);
 
+/* a2 + a3 + a4 in one pass: the whole product C = A * B after spgemm_plan, without the separate
+ * symbolic pass.  As in Section IV-B, C is allocated once from the never-underestimating estimate
+ * (the multiplication count F of spgemm_plan_info) and rows are appended in order: every tile
+ * of 32 rows finds its offset in C from the tiles before it (decoupled look-back).
+ *   A_val, B_val -- device values aligned with A's and B's entries.
+ *   C_row_ptr    -- device, A.rows + 1 int32, written with C's row pointer.
+ *   C_col, C_val -- device, `capacity` entries each; capacity >= F always suffices.
+ *   nnz_c        -- host, receives nnz(C).
+ * Enqueues on stream and synchronises it.  Errors: STATE, INVALID, OVERFLOW (nnz(C) > capacity or
+ * > INT32_MAX; C's contents are then incomplete), TABLE_FULL, TIMEOUT, CUDA.  After it, the plan is
+ * in the same state as after spgemm_symbolic: spgemm_numeric can recompute values in place. */
+spgemm_status_t spgemm_compute(spgemm_plan_t plan, const double* A_val, const double* B_val, int32_t* C_row_ptr,
+                               int32_t* C_col, double* C_val, int64_t capacity, int64_t* nnz_c, void* stream);
+
 /* Synchronise stream and report the plan's sticky device status (OK or the first error). */
 spgemm_status_t spgemm_status(spgemm_plan_t plan, void* stream);
 
 /* Copy the plan's counters (host-side copies; no synchronisation). */
 spgemm_status_t spgemm_plan_info(spgemm_plan_t plan, spgemm_info_t* info);
+
+/* Optional timing hook: two cudaEvent_t created by the caller (or both NULL to clear).  From now on
+ * spgemm_numeric and spgemm_compute record start_event on their stream right before their first
+ * compute kernel and stop_event right after their last one, so a caller can time the kernels
+ * without the host synchronisation that spgemm_compute performs.  Errors: INVALID. */
+spgemm_status_t spgemm_plan_set_events(spgemm_plan_t plan, void* start_event, void* stop_event);
 
 /* Release the plan object.  The workspace stays the caller's.  NULL is accepted. */
 spgemm_status_t spgemm_free(spgemm_plan_t plan);

@@ -60,7 +60,7 @@ def _load():
             lib.oracle_flops.argtypes = [i64, i64, _I64P, _I64P, _I64P]
             lib.oracle_spgemm.restype = i64
             lib.oracle_spgemm.argtypes = [i64, i64, i64, _I64P, _I64P, _F64P, _I64P, _I64P, _F64P,
-                                          i64, _I64P, _I64P, _F64P, _F64P, _I64P]
+                                          i64, _I64P, _I64P, _F64P, _F64P, _I64P, _I64P]
             lib.oracle_grad.restype = ctypes.c_int
             lib.oracle_grad.argtypes = [i64, i64, i64, _I64P, _I64P, _F64P, _I64P, _I64P, _F64P,
                                         _I64P, _I64P, _F64P, _F64P, _F64P]
@@ -91,7 +91,10 @@ def flops(A, B) -> int:
 
 
 def spgemm(A, B) -> dict:
-    """C = A*B.  Returns dict(row_ptr, col_idx, val, absval, u, F, nnz, rows, cols), int64 indices."""
+    """C = A*B.  Returns dict(row_ptr, col_idx, val, absval, count, u, F, nnz, rows, cols), int64 indices.
+
+    absval is the sum of |a*b| of each entry (the scale of its rounding error), count the
+    number of products in it."""
     _check(A, B)
     lib = _load()
     Arp, Acol, Aval = _i64(A.row_ptr), _i64(A.col_idx), _f64(A.val)
@@ -102,13 +105,15 @@ def spgemm(A, B) -> dict:
     Ccol = np.empty(cap, np.int64)
     Cval = np.empty(cap, np.float64)
     Cabs = np.empty(cap, np.float64)
+    Ccnt = np.empty(cap, np.int64)
     u = np.zeros(max(A.rows, 1), np.int64)
     nnz = int(lib.oracle_spgemm(A.rows, A.cols, B.cols, Arp, Acol, Aval, Brp, Bcol, Bval,
-                                cap, Crp, Ccol, Cval, Cabs, u))
+                                cap, Crp, Ccol, Cval, Cabs, Ccnt, u))
     if nnz < 0:
         raise RuntimeError(f"oracle_spgemm failed ({nnz})")
     return dict(rows=A.rows, cols=B.cols, row_ptr=Crp, col_idx=Ccol[:nnz].copy(),
-                val=Cval[:nnz].copy(), absval=Cabs[:nnz].copy(), u=u[:A.rows].copy(), F=F, nnz=nnz)
+                val=Cval[:nnz].copy(), absval=Cabs[:nnz].copy(), count=Ccnt[:nnz].copy(), u=u[:A.rows].copy(),
+                F=F, nnz=nnz)
 
 
 def grad(A, B, C: dict, W) -> tuple[np.ndarray, np.ndarray]:

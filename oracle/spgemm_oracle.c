@@ -55,21 +55,22 @@ int64_t oracle_flops(int64_t m, int64_t k, const int64_t* A_rp, const int64_t* A
 /*
  * C = A * B.  A is m x k, B is k x n.  Outputs:
  *   C_rp[m+1], C_col[cap], C_val[cap], C_abs[cap] (sum of |a*b| per entry),
- *   u[m] (multiplications of each row).
+ *   C_cnt[cap] (number of products in each entry), u[m] (multiplications of each row).
  * Returns nnz(C), or -1 if cap is too small, -2 on allocation failure.
  */
 int64_t oracle_spgemm(int64_t m, int64_t k, int64_t n,
                       const int64_t* A_rp, const int64_t* A_col, const double* A_val,
                       const int64_t* B_rp, const int64_t* B_col, const double* B_val,
                       int64_t cap, int64_t* C_rp, int64_t* C_col, double* C_val,
-                      double* C_abs, int64_t* u) {
+                      double* C_abs, int64_t* C_cnt, int64_t* u) {
     (void)k;
     double* temp = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
     double* tabs = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    int64_t* tcnt = (int64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
     char* flag = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
     int64_t* list = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
-    if (!temp || !tabs || !flag || !list) {
-        free(temp); free(tabs); free(flag); free(list);
+    if (!temp || !tabs || !tcnt || !flag || !list) {
+        free(temp); free(tabs); free(tcnt); free(flag); free(list);
         return -2;
     }
     int64_t nnz = 0;
@@ -88,13 +89,14 @@ int64_t oracle_spgemm(int64_t m, int64_t k, int64_t n,
                 }
                 temp[x] += prod;
                 tabs[x] += fabs(prod);
+                tcnt[x] += 1;
                 ++mults;
             }
         }
         u[r] = mults;
         qsort(list, (size_t)len, sizeof(int64_t), cmp_i64);
         if (nnz + len > cap) {
-            free(temp); free(tabs); free(flag); free(list);
+            free(temp); free(tabs); free(tcnt); free(flag); free(list);
             return -1;
         }
         for (int64_t t = 0; t < len; ++t) {
@@ -102,14 +104,16 @@ int64_t oracle_spgemm(int64_t m, int64_t k, int64_t n,
             C_col[nnz] = x;
             C_val[nnz] = temp[x];
             C_abs[nnz] = tabs[x];
+            C_cnt[nnz] = tcnt[x];
             ++nnz;
             temp[x] = 0.0;
             tabs[x] = 0.0;
+            tcnt[x] = 0;
             flag[x] = 0;
         }
         C_rp[r + 1] = nnz;
     }
-    free(temp); free(tabs); free(flag); free(list);
+    free(temp); free(tabs); free(tcnt); free(flag); free(list);
     return nnz;
 }
 

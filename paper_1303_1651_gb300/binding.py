@@ -69,14 +69,17 @@ def load():
                                     ctypes.c_size_t, vp]
         lib.spgemm_symbolic.argtypes = [vp, vp, P(ctypes.c_int64), vp]
         lib.spgemm_numeric.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.spgemm_compute.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int64, P(ctypes.c_int64), vp]
         lib.spgemm_status.argtypes = [vp, vp]
+        lib.spgemm_plan_set_events.argtypes = [vp, vp, vp]
         lib.spgemm_plan_info.argtypes = [vp, P(spgemm_info_t)]
         lib.spgemm_free.argtypes = [vp]
         lib.spgemm_error_string.argtypes = [ctypes.c_int]
         lib.spgemm_error_string.restype = ctypes.c_char_p
         lib.spgemm_version.restype = ctypes.c_int32
         for name in ("spgemm_workspace_size", "spgemm_plan", "spgemm_symbolic", "spgemm_numeric",
-                     "spgemm_status", "spgemm_plan_info", "spgemm_free"):
+                     "spgemm_compute", "spgemm_status", "spgemm_plan_info", "spgemm_free",
+                     "spgemm_plan_set_events"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -173,6 +176,15 @@ def spgemm_numeric(plan: int, A_val: torch.Tensor, B_val: torch.Tensor, C_col: t
            "spgemm_numeric")
 
 
+def spgemm_compute(plan: int, A_val: torch.Tensor, B_val: torch.Tensor, C_row_ptr: torch.Tensor,
+                   C_col: torch.Tensor, C_val: torch.Tensor, stream=None) -> int:
+    nnz = ctypes.c_int64(0)
+    cap = min(C_col.numel(), C_val.numel())
+    _check(load().spgemm_compute(plan, _ptr(A_val), _ptr(B_val), C_row_ptr.data_ptr(), _ptr(C_col), _ptr(C_val),
+                                 cap, ctypes.byref(nnz), _stream(stream)), "spgemm_compute")
+    return int(nnz.value)
+
+
 def spgemm_status(plan: int, stream=None):
     _check(load().spgemm_status(plan, _stream(stream)), "spgemm_status")
 
@@ -182,6 +194,16 @@ def spgemm_plan_info(plan: int) -> dict:
     _check(load().spgemm_plan_info(plan, ctypes.byref(info)), "spgemm_plan_info")
     return dict(products=int(info.products), nnz_c=int(info.nnz_c), max_row_products=int(info.max_row_products),
                 rows_per_class=dict(zip(CLASS_NAMES, list(info.rows_per_class))))
+
+
+def spgemm_plan_set_events(plan: int, start=None, stop=None):
+    """Record torch.cuda.Event objects (timing enabled) around the plan's compute kernels."""
+    # torch creates the CUDA event on its first record(): record once so the handles exist
+    for ev in (start, stop):
+        if ev is not None:
+            ev.record()
+    _check(load().spgemm_plan_set_events(plan, start.cuda_event if start is not None else None,
+                                         stop.cuda_event if stop is not None else None), "spgemm_plan_set_events")
 
 
 def spgemm_free(plan: int):
@@ -243,3 +265,24 @@ def multiply(A: DeviceCSR, B: DeviceCSR, opt: spgemm_options_t | None = None, st
         return C
     finally:
         prod.close()
+
+
+def multiply_fused(A: DeviceCSR, B: DeviceCSR, opt: spgemm_options_t | None = None, stream=None,
+                   workspace: torch.Tensor | None = None, trim: bool = True) -> DeviceCSR:
+    """C = A*B through plan and the single-pass spgemm_compute (C sized by the multiplication count)."""
+    dev = A.row_ptr.device
+    need = spgemm_workspace_size(A, B, opt)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    plan = spgemm_plan(A, B, workspace, opt, stream)
+    try:
+        F = spgemm_plan_info(plan)["products"]
+        C_rp = torch.empty(A.rows + 1, dtype=torch.int32, device=dev)
+        C_col = torch.empty(max(F, 1), dtype=torch.int32, device=dev)
+        C_val = torch.empty(max(F, 1), dtype=torch.float64, device=dev)
+        nnz = spgemm_compute(plan, A.val, B.val, C_rp, C_col, C_val, stream)
+    finally:
+        spgemm_free(plan)
+    if trim:
+        C_col, C_val = C_col[:nnz], C_val[:nnz]
+    return DeviceCSR(A.rows, B.cols, C_rp, C_col, C_val)

@@ -15,7 +15,7 @@ constexpr size_t ALIGN = 256;
 inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t ctr, cls, list_w, list_b, list_g, scan, slabs, total;
+  size_t ctr, cls, list_w, list_b, list_g, scan, fused, slabs, total;
 };
 
 Layout layout(int m, int ncols, int nslabs) {
@@ -27,6 +27,7 @@ Layout layout(int m, int ncols, int nslabs) {
   L.list_b = o; o += up(4 * (size_t)std::max(m, 1));
   L.list_g = o; o += up(4 * (size_t)std::max(m, 1));
   L.scan = o; o += up(scan_tile_state_bytes((long long)m + 1) + 64);
+  L.fused = o; o += up(fused_tile_state_bytes(m) + 64);
   L.slabs = o; o += (size_t)nslabs * dense_slab_bytes(ncols);
   L.total = o;
   return L;
@@ -98,6 +99,7 @@ struct spgemm_plan_s {
   int state = 0;                // 1 planned, 2 symbolic done
   int32_t* C_rp = nullptr;
   bool slabs_clean = false;
+  cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // optional, recorded around the compute kernels
 };
 
 extern "C" {
@@ -114,7 +116,7 @@ const char* spgemm_error_string(int code) {
     case SPGEMM_ERR_CUDA: return "CUDA error";
     case SPGEMM_ERR_TIMEOUT: return "bounded device wait timed out";
     case SPGEMM_ERR_STATE: return "calls out of order";
-    case SPGEMM_ERR_UNSORTED: return "rows of B must be sorted by column";
+    case SPGEMM_ERR_UNSORTED: return "reserved: unsorted input";
     case SPGEMM_ERR_MISMATCH: return "structure changed between symbolic and numeric";
     default: return "unknown status";
   }
@@ -185,8 +187,8 @@ spgemm_status_t spgemm_symbolic(spgemm_plan_t p, int32_t* C_row_ptr, int64_t* nn
     cudaMemsetAsync(p->ws + L.slabs, 0, (size_t)p->nslabs * dense_slab_bytes(p->B.cols), s);
     p->slabs_clean = true;
   }
-  if (cnt[CLS_M1] > 0) launch_merge_symbolic(CLS_M1, p->A, p->B, cls, C_row_ptr, p->ctr, s);
-  if (cnt[CLS_M2] > 0) launch_merge_symbolic(CLS_M2, p->A, p->B, cls, C_row_ptr, p->ctr, s);
+  const int wide = p->h.max_u_merge > 32;
+  if (cnt[CLS_M1] + cnt[CLS_M2] > 0) launch_merge_symbolic(wide, p->A, p->B, cls, C_row_ptr, p->ctr, s);
   if (cnt[CLS_W] > 0)
     launch_hash_symbolic(CLS_W, p->A, p->B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s);
   if (cnt[CLS_B] > 0)
@@ -217,8 +219,9 @@ spgemm_status_t spgemm_numeric(spgemm_plan_t p, const double* A_val, const doubl
   const Layout& L = p->L;
   const int* cnt = p->h.count;
   uint8_t* cls = p->ws + L.cls;
-  if (cnt[CLS_M1] > 0) launch_merge_numeric(CLS_M1, A, B, cls, p->C_rp, C_col, C_val, p->ctr, s);
-  if (cnt[CLS_M2] > 0) launch_merge_numeric(CLS_M2, A, B, cls, p->C_rp, C_col, C_val, p->ctr, s);
+  const int wide = p->h.max_u_merge > 32;
+  if (p->ev_start) cudaEventRecord(p->ev_start, s);
+  if (cnt[CLS_M1] + cnt[CLS_M2] > 0) launch_merge_numeric(wide, A, B, cls, p->C_rp, C_col, C_val, p->ctr, s);
   if (cnt[CLS_W] > 0)
     launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s);
   if (cnt[CLS_B] > 0)
@@ -226,7 +229,67 @@ spgemm_status_t spgemm_numeric(spgemm_plan_t p, const double* A_val, const doubl
   if (cnt[CLS_G] > 0)
     launch_dense_numeric(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs, p->C_rp,
                          C_col, C_val, p->ctr, s);
+  if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
   if (cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_compute(spgemm_plan_t p, const double* A_val, const double* B_val, int32_t* C_row_ptr,
+                               int32_t* C_col, double* C_val, int64_t capacity, int64_t* nnz_c, void* stream) {
+  if (!p || p->state < 1) return SPGEMM_ERR_STATE;
+  if (!C_row_ptr || !nnz_c || capacity < 0) return SPGEMM_ERR_INVALID;
+  if ((!A_val && p->A.nnz > 0) || (!B_val && p->B.nnz > 0)) return SPGEMM_ERR_INVALID;
+  if ((!C_col || !C_val) && capacity > 0) return SPGEMM_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Layout& L = p->L;
+  const int m = p->A.rows;
+  DevCsr A = p->A, B = p->B;
+  A.val = A_val;
+  B.val = B_val;
+  if (m == 0) {
+    cudaMemsetAsync(C_row_ptr, 0, sizeof(int32_t), s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SPGEMM_ERR_CUDA;
+    *nnz_c = 0;
+    p->C_rp = C_row_ptr;
+    p->h.nnzC = 0;
+    p->state = 2;
+    return SPGEMM_OK;
+  }
+  const int* cnt = p->h.count;
+  uint8_t* cls = p->ws + L.cls;
+  cudaMemsetAsync(&p->ctr->ticket, 0, sizeof(unsigned), s);
+  cudaMemsetAsync(p->ws + L.fused, 0, fused_tile_state_bytes(m), s);
+  // rows of the hash and dense classes: counts first (the fused pass places every row)
+  if (cnt[CLS_G] > 0 && !p->slabs_clean) {
+    cudaMemsetAsync(p->ws + L.slabs, 0, (size_t)p->nslabs * dense_slab_bytes(p->B.cols), s);
+    p->slabs_clean = true;
+  }
+  if (p->ev_start) cudaEventRecord(p->ev_start, s);
+  if (cnt[CLS_W] > 0)
+    launch_hash_symbolic(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s);
+  if (cnt[CLS_B] > 0)
+    launch_hash_symbolic(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s);
+  if (cnt[CLS_G] > 0)
+    launch_dense_symbolic(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs,
+                          C_row_ptr, p->ctr, s);
+  const int wide = p->h.max_u_merge > 32;
+  launch_merge_fused(wide, A, B, cls, C_row_ptr, C_col, C_val, capacity,
+                     (unsigned long long*)(p->ws + L.fused), p->ctr, s);
+  if (cnt[CLS_W] > 0)
+    launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, C_col, C_val, p->ctr, s);
+  if (cnt[CLS_B] > 0)
+    launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, C_col, C_val, p->ctr, s);
+  if (cnt[CLS_G] > 0)
+    launch_dense_numeric(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs, C_row_ptr,
+                         C_col, C_val, p->ctr, s);
+  if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
+  cudaMemcpyAsync(&p->h, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  const spgemm_status_t st = status_from_bits(p->h.status);
+  if (st != SPGEMM_OK) return st;
+  p->C_rp = C_row_ptr;
+  p->state = 2;
+  *nnz_c = p->h.nnzC;
   return SPGEMM_OK;
 }
 
@@ -245,6 +308,13 @@ spgemm_status_t spgemm_plan_info(spgemm_plan_t p, spgemm_info_t* info) {
   info->nnz_c = p->state >= 2 ? p->h.nnzC : -1;
   info->max_row_products = p->h.max_u;
   for (int i = 0; i < NUM_CLS; ++i) info->rows_per_class[i] = p->h.count[i];
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_plan_set_events(spgemm_plan_t p, void* start_event, void* stop_event) {
+  if (!p || ((start_event == nullptr) != (stop_event == nullptr))) return SPGEMM_ERR_INVALID;
+  p->ev_start = (cudaEvent_t)start_event;
+  p->ev_stop = (cudaEvent_t)stop_event;
   return SPGEMM_OK;
 }
 

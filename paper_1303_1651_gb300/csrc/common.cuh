@@ -47,7 +47,8 @@ struct Counters {
   unsigned ticket;           // scan tile ticket
   int count[NUM_CLS];        // rows per class
   int max_u;                 // largest row product count
-  int pad[6];
+  int max_u_merge;           // largest product count among merge-class rows
+  int pad[5];
 };
 
 struct Limits {
@@ -63,6 +64,19 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 __device__ __forceinline__ unsigned lanemask_le() {
   unsigned m; asm("mov.u32 %0, %%lanemask_le;" : "=r"(m)); return m;
+}
+
+// Asynchronous global -> shared copies (LDGSTS), 4 and 8 bytes; the source must be aligned to the size.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Exclusive warp scan of an int; *total receives the warp sum.

@@ -14,11 +14,18 @@ void launch_bin(const DevCsr& A, const DevCsr& B, const Limits& lim, uint8_t* cl
 size_t scan_tile_state_bytes(long long n);
 void launch_scan(int* rp, long long n, unsigned long long* tile_state, Counters* ctr, cudaStream_t s);
 
-// a2/a4, merge classes: warp tiles of 32 consecutive rows, rows of class `cls` only.
-void launch_merge_symbolic(int cls, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* counts,
+// a2/a4, merge classes (M1 and M2 together): warp tiles of 32 consecutive rows.  `wide` selects the
+// 64-product sort (needed when some merge-class row has more than 32 products).
+void launch_merge_symbolic(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* counts,
                            Counters* ctr, cudaStream_t s);
-void launch_merge_numeric(int cls, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, const int* rp,
+void launch_merge_numeric(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, const int* rp,
                           int* C_col, double* C_val, Counters* ctr, cudaStream_t s);
+// Fused single pass: numeric for merge-class rows, C's row pointer for every row (rows of other classes
+// bring their counts in rp), entries written into C_col/C_val of `capacity` entries.  Uses ctr->ticket.
+void launch_merge_fused(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* rp, int* C_col,
+                        double* C_val, long long capacity, unsigned long long* tile_state, Counters* ctr,
+                        cudaStream_t s);
+size_t fused_tile_state_bytes(int rows);
 
 // a2/a4, hash classes W (warp per row) and B (block per row), rows from a list.
 void launch_hash_symbolic(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts,
@@ -34,5 +41,8 @@ void launch_dense_numeric(const DevCsr& A, const DevCsr& B, const int* list, int
                           const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s);
 
 int num_sms();
+
+// Largest B.cols the merge classes accept (their sort keys hold column << 6).
+int merge_max_cols();
 
 }  // namespace spg

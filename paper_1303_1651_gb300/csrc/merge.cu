@@ -1,234 +1,443 @@
-// a2 symbolic and a4 numeric for rows with few, short contributions (classes M1, M2).
+// a2 symbolic, a4 numeric, and the fused single pass, for rows with few, short
+// contributions (classes M1 and M2: at most 8 entries of A, at most 64 products).
 //
 // The row-major algorithm of Section IV-A builds row r of C from the rows B_j
-// (j in row r of A) scaled by a_rj.  With every B_j sorted by column, row r of
-// C is the merge of those k sorted runs, and merging produces the columns in
-// ascending order directly -- the "Sort" store of Section IV-B without a sort,
-// and the paper's future-work item of a cheaper ordering for short lists.
+// (j in row r of A) scaled by a_rj.  Its dense temporary vector is replaced here
+// by the products of the row themselves, held in registers and put in column
+// order by a sorting network -- the "Sort" store of Section IV-B, with the
+// short-list sort the paper's conclusion asks for.
 //
-// One warp owns a tile of 32 consecutive rows; lane t owns row tile*32+t.
-//   1. run table   -- lane t gathers its <= 8 runs (A entry -> B row range).
-//   2. expand      -- the warp copies every run element into shared memory with
-//                     lane-parallel, coalesced loads (lanes walk the products of
-//                     the tile; a redux.or of run-start bits gives each lane its
-//                     run).  The numeric pass multiplies a_rj * b_jx here, once
-//                     per product, with every lane busy.
-//   3. merge       -- lane t merges its runs from shared memory.  Equal columns
-//                     are combined in run order, and within a run in storage
-//                     order, i.e. in exactly the order of the dense-accumulator
-//                     loop, starting from the first product (no add to zero).
-//   4. write       -- (numeric) outputs go through a small per-lane buffer of 8
-//                     entries that the warp flushes cooperatively, so stores to
-//                     C are coalesced per row segment.
+// One warp owns a tile of 32 consecutive rows; lane t owns row tile*32 + t,
+// whose u_t <= N products (N = 32 or 64, chosen per matrix from the longest
+// merge-class row) come from at most 8 entries of A.
+//   1. run table   -- lane t gathers its runs (A entry -> B row range).
+//   2. expand      -- the warp copies every product's column (and b_jx) into
+//                     shared memory with lane-parallel, coalesced cp.async copies,
+//                     the whole tile in flight at once.  Lanes walk the tile's
+//                     product space; a redux.or of run-start bits names each
+//                     lane's run.  Layout [j][t] with an XOR swizzle: conflict-free
+//                     for these writes (fixed t, consecutive j) and for the
+//                     per-lane reads below (fixed j).  Then each lane multiplies
+//                     its staged b_jx by a_rj, one multiply per product.
+//   3. sort        -- lane t loads keys (column << log2 N | product index) into
+//                     registers and runs a bitonic network.  Equal columns end up
+//                     adjacent, ordered by product index: the order of the
+//                     dense-accumulator loop.
+//   4. count       -- distinct columns of the row (symbolic result).
+//   5. reduce      -- sums each group of equal columns in that order, first
+//                     product stored and the rest added, and leaves the sum in the
+//                     slot of the group's last product (already read); the group's
+//                     key goes to the tile's flat output list.
+//   6. place       -- numeric: C's row pointer is known.  Fused: the tile publishes
+//                     its entry count and finds its offset in C by a decoupled
+//                     look-back over the preceding tiles (the streaming append of
+//                     Section IV-B: one allocation sized by the multiplication
+//                     count, rows appended in order), then writes C's row pointers.
+//   7. write       -- consecutive lanes store consecutive entries of C.
+// Rows of B need not be sorted: the network orders everything.  Keys need
+// column < 2^26 - 1; wider matrices use the hash classes.
 #include "internal.h"
 
 namespace spg {
 
-constexpr int MERGE_K = 8;                 // max runs per row (A entries)
-constexpr int MAXR = 32 * MERGE_K;         // run table entries per tile
-constexpr int FSTRIDE = 9;                 // flush buffer row stride (odd: no bank conflicts)
-constexpr int FDEPTH = 8;                  // outputs buffered per lane before a flush
+constexpr int MERGE_K = 8;            // max runs (A entries) per row
+constexpr int MAXR = 32 * MERGE_K;    // run-table entries per tile
+constexpr long long FUSED_SPIN_LIMIT = 1LL << 24;
 
-template <bool NUM, int PCAP>
-struct MergeSmem {
-  // doubles first (8-byte alignment), then ints
-  static constexpr size_t s_val = 0;
-  static constexpr size_t r_a = s_val + (NUM ? 8 * PCAP : 0);
-  static constexpr size_t f_val = r_a + (NUM ? 8 * MAXR : 0);
-  static constexpr size_t s_col = f_val + (NUM ? 8 * 32 * FSTRIDE : 0);
-  static constexpr size_t r_src = s_col + 4 * PCAP;
-  static constexpr size_t r_dst = r_src + 4 * MAXR;
-  static constexpr size_t f_col = r_dst + 4 * MAXR;
-  static constexpr size_t bytes = f_col + (NUM ? 4 * 32 * FSTRIDE : 0) + 16;
+enum MergeMode { MODE_SYM = 0, MODE_NUM = 1, MODE_FUSED = 2 };
+
+template <int MODE, int N>
+struct SortSmem {
+  // Staging: row t's products are contiguous, at pofs_t + t (one slot of skew per row keeps
+  // lanes that read the same position of their rows on different banks).
+  static constexpr int SLOTS = 32 * N + 32;
+  static constexpr bool V = MODE != MODE_SYM;
+  static constexpr size_t s_val = 0;                               // double [SLOTS]  b_jx, later group sums
+  static constexpr size_t s_col = s_val + (V ? 8 * SLOTS : 0);     // uint   [SLOTS]  columns, later output keys
+  static constexpr size_t r_run = s_col + 4 * SLOTS;               // int2   [MAXR]   (first B entry, start << 8 | lane)
+  static constexpr size_t bytes = r_run + 8 * MAXR;                // s_a (double [8][32], a_rj by run rank and
+                                                                   // lane) reuses r_run after the expand
+  static_assert(8 * 8 * 32 <= 8 * MAXR, "a table must fit in the run table");
 };
 
-template <bool NUM, int PCAP, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
-k_merge(DevCsr A, DevCsr B, const uint8_t* __restrict__ rowcls, int cls, const int* __restrict__ rp,
-        int* __restrict__ counts, int* __restrict__ C_col, double* __restrict__ C_val, Counters* __restrict__ ctr) {
-  using L = MergeSmem<NUM, PCAP>;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* wb = smem + (size_t)warp * L::bytes;
-  double* s_val = reinterpret_cast<double*>(wb + L::s_val);
-  double* r_a = reinterpret_cast<double*>(wb + L::r_a);
-  double* f_val = reinterpret_cast<double*>(wb + L::f_val);
-  int* s_col = reinterpret_cast<int*>(wb + L::s_col);
-  int* r_src = reinterpret_cast<int*>(wb + L::r_src);
-  int* r_dst = reinterpret_cast<int*>(wb + L::r_dst);
-  int* f_col = reinterpret_cast<int*>(wb + L::f_col);
-
-  const int ntiles = (A.rows + 31) >> 5;
-  for (int tile = blockIdx.x * WARPS + warp; tile < ntiles; tile += gridDim.x * WARPS) {
-    const int r = tile * 32 + lane;
-    const bool mine = r < A.rows && rowcls[r] == cls;
-    if (!__any_sync(FULL, mine)) continue;
-
-    // 1. run table
-    int a0 = 0, k = 0;
-    if (mine) { a0 = A.rp[r]; k = A.rp[r + 1] - a0; }
-    int src[MERGE_K], len[MERGE_K];
-    double av[MERGE_K];
-    int u = 0, nz = 0;
+template <int N>
+__device__ __forceinline__ void bitonic_sort(unsigned (&k)[N]) {
 #pragma unroll
-    for (int i = 0; i < MERGE_K; ++i) {
-      len[i] = 0; src[i] = 0; av[i] = 0.0;
-      if (i < k) {
-        const int j = __ldg(A.col + a0 + i);
-        const int bs = __ldg(B.rp + j);
-        len[i] = __ldg(B.rp + j + 1) - bs;
-        src[i] = bs;
-        if (NUM) av[i] = __ldg(A.val + a0 + i);
-        u += len[i];
-        nz += len[i] > 0;
-      }
-    }
-    int P, R;
-    const int pofs = warp_excl_scan(u, &P);   // P <= PCAP: class limits bound every row
-    const int rofs = warp_excl_scan(nz, &R);
-    int dst[MERGE_K];
-    {
-      int d = pofs, q = rofs;
+  for (int size = 2; size <= N; size <<= 1) {
 #pragma unroll
-      for (int i = 0; i < MERGE_K; ++i) {
-        dst[i] = d;
-        if (len[i] > 0) {
-          r_src[q] = src[i];
-          r_dst[q] = d;
-          if (NUM) r_a[q] = av[i];
-          ++q;
-          d += len[i];
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const unsigned a = k[i], b = k[j];
+          const unsigned lo = min(a, b), hi = max(a, b);
+          if ((i & size) == 0) { k[i] = lo; k[j] = hi; } else { k[i] = hi; k[j] = lo; }
         }
       }
     }
-    __syncwarp();
-
-    // 2. expand: position p of the tile's product space belongs to the last run starting at or before p
-    int e_cur = 0;
-    for (int base = 0; base < P; base += 32) {
-      const int cand = e_cur + 1 + lane;
-      const int s = cand < R ? r_dst[cand] : KEY_NONE;
-      const unsigned off = (unsigned)(s - base);
-      const unsigned bit = off < 32u ? (1u << off) : 0u;
-      const unsigned M = __reduce_or_sync(FULL, bit);
-      const int e = e_cur + __popc(M & lanemask_le());
-      const int p = base + lane;
-      if (p < P) {
-        const int sp = r_src[e] + (p - r_dst[e]);
-        s_col[p] = __ldg(B.col + sp);
-        if (NUM) s_val[p] = __dmul_rn(r_a[e], __ldg(B.val + sp));
-      }
-      e_cur = __shfl_sync(FULL, e, 31);
-    }
-    __syncwarp();
-
-    // 3. merge the runs of this lane's row
-    int h[MERGE_K], cur[MERGE_K], end[MERGE_K];
-#pragma unroll
-    for (int i = 0; i < MERGE_K; ++i) {
-      cur[i] = dst[i];
-      end[i] = dst[i] + len[i];
-      h[i] = len[i] > 0 ? s_col[cur[i]] : KEY_NONE;
-    }
-    bool unsorted = false;
-    if (!NUM) {
-      int cnt = 0, last = -1;
-      while (true) {
-        int m = h[0];
-#pragma unroll
-        for (int i = 1; i < MERGE_K; ++i) m = min(m, h[i]);
-        if (m == KEY_NONE) break;
-        cnt += (m != last);
-        last = m;
-#pragma unroll
-        for (int i = 0; i < MERGE_K; ++i) {
-          if (h[i] == m) {
-            ++cur[i];
-            h[i] = cur[i] < end[i] ? s_col[cur[i]] : KEY_NONE;
-            unsorted |= h[i] < m;
-          }
-        }
-      }
-      if (mine) counts[r] = cnt;
-    } else {
-      int g = 0, gend = 0;
-      if (mine) { g = rp[r]; gend = rp[r + 1]; }
-      int cnt = 0;
-      auto flush = [&]() {
-        __syncwarp();
-#pragma unroll
-        for (int jj = 0; jj < FDEPTH; ++jj) {
-          const int t = (lane >> 3) + 4 * jj, s = lane & 7;
-          const int ct = __shfl_sync(FULL, cnt, t);
-          const int gt = __shfl_sync(FULL, g, t);
-          const int et = __shfl_sync(FULL, gend, t);
-          if (s < ct && gt + s < et) {
-            C_col[gt + s] = f_col[t * FSTRIDE + s];
-            C_val[gt + s] = f_val[t * FSTRIDE + s];
-          }
-        }
-        g += cnt;
-        cnt = 0;
-        __syncwarp();
-      };
-      while (true) {
-        int m = h[0];
-#pragma unroll
-        for (int i = 1; i < MERGE_K; ++i) m = min(m, h[i]);
-        const bool act = m != KEY_NONE;
-        if (!__any_sync(FULL, act)) break;
-        if (act) {
-          double v = 0.0;
-          bool first = true;
-#pragma unroll
-          for (int i = 0; i < MERGE_K; ++i) {
-            while (h[i] == m) {
-              const double x = s_val[cur[i]];
-              if (first) v = x; else v = __dadd_rn(v, x);
-              first = false;
-              ++cur[i];
-              h[i] = cur[i] < end[i] ? s_col[cur[i]] : KEY_NONE;
-            }
-            unsorted |= h[i] < m;
-          }
-          f_col[lane * FSTRIDE + cnt] = m;
-          f_val[lane * FSTRIDE + cnt] = v;
-          ++cnt;
-        }
-        if (__any_sync(FULL, cnt == FDEPTH)) flush();
-      }
-      if (__any_sync(FULL, cnt > 0)) flush();
-      if (mine && g != gend) atomicOr(&ctr->status, ST_MISMATCH);
-    }
-    if (unsorted) atomicOr(&ctr->status, ST_UNSORTED);
-    __syncwarp();
   }
 }
 
-template <bool NUM, int PCAP, int WARPS>
-static void launch_merge(const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int cls, const int* rp,
-                         int* counts, int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
-  constexpr size_t bytes = (size_t)WARPS * MergeSmem<NUM, PCAP>::bytes;
-  auto kern = k_merge<NUM, PCAP, WARPS>;
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
+// Decoupled look-back over tiles.  State word: value << 2 | flag, flag 1 = the tile's own total,
+// 2 = inclusive prefix.  A tile publishes its total as soon as it is known (tile_publish), does
+// other work, then (tile_lookback) reads 32 predecessors per step, adds totals back to the
+// nearest inclusive prefix and publishes its own.  Every wait is bounded (ST_TIMEOUT).
+__device__ __forceinline__ void tile_publish(unsigned long long* ts, int tile, long long total) {
+  if ((threadIdx.x & 31) == 0) atomicExch(&ts[tile], ((unsigned long long)total << 2) | (tile == 0 ? 2ull : 1ull));
+}
+
+__device__ long long tile_lookback(unsigned long long* ts, int tile, long long total, Counters* ctr) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) return 0;
+  long long prefix = 0;
+  int pred = tile - 1;
+  bool timed_out = false;
+  while (true) {
+    const int p = pred - lane;
+    unsigned long long w = 2ull;   // before tile 0: an inclusive prefix of 0
+    if (p >= 0) {
+      long long spins = 0;
+      w = ld_volatile_u64(&ts[p]);
+      while ((w & 3ull) == 0ull) {
+        if (++spins > FUSED_SPIN_LIMIT) { timed_out = true; w = 2ull; break; }
+        __nanosleep(32);
+        w = ld_volatile_u64(&ts[p]);
+      }
+    }
+    const unsigned incl = __ballot_sync(FULL, (w & 3ull) == 2ull);
+    if (incl) {
+      const int L = __ffs(incl) - 1;          // nearest predecessor with an inclusive prefix
+      prefix += warp_sum_ll(lane <= L ? (long long)(w >> 2) : 0LL);
+      break;
+    }
+    prefix += warp_sum_ll((long long)(w >> 2));
+    pred -= 32;
+  }
+  if (__any_sync(FULL, timed_out) && lane == 0) atomicOr(&ctr->status, ST_TIMEOUT);
+  if (lane == 0) atomicExch(&ts[tile], ((unsigned long long)(prefix + total) << 2) | 2ull);
+  return prefix;
+}
+
+struct MergeArgs {
+  DevCsr A, B;
+  const uint8_t* rowcls;
+  int* rp;                       // SYM: counts out; NUM: C row pointer in; FUSED: counts of other classes in, row pointer out
+  int* C_col;
+  double* C_val;
+  long long capacity;            // FUSED: entries available in C_col / C_val
+  unsigned long long* tile_state;
+  Counters* ctr;
+};
+
+template <int MODE, int N, int WARPS>
+__device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigned char* wb) {
+  using L = SortSmem<MODE, N>;
+  constexpr bool V = L::V;
+  constexpr int IB = (N == 32) ? 5 : 6;     // product-index bits of a key
+  constexpr int KB = IB + 3;                // + run-index bits: key = col << KB | run << IB | index
+  constexpr unsigned PAD = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  double* s_val = reinterpret_cast<double*>(wb + L::s_val);
+  unsigned* s_col = reinterpret_cast<unsigned*>(wb + L::s_col);
+  int2* r_run = reinterpret_cast<int2*>(wb + L::r_run);
+  double* s_a = reinterpret_cast<double*>(wb + L::r_run);
+  const DevCsr& A = g.A;
+  const DevCsr& B = g.B;
+
+  const int r = tile * 32 + lane;
+  const bool inrange = r < A.rows;
+  const int c = inrange ? (int)g.rowcls[r] : -1;
+  const bool mine = c == CLS_M1 || c == CLS_M2;
+  if (MODE != MODE_FUSED && !__any_sync(FULL, mine)) return;
+
+  // 1. run table
+  int a0 = 0, k = 0;
+  if (mine) { a0 = __ldg(A.rp + r); k = __ldg(A.rp + r + 1) - a0; }
+  int other = 0;    // FUSED: entry count of a row of another class (from its symbolic pass)
+  if (MODE == MODE_FUSED && inrange && !mine) other = g.rp[r];
+  int gbeg = 0, gend = 0;   // NUM: C's row range
+  if (MODE == MODE_NUM && mine) { gbeg = __ldg(g.rp + r); gend = __ldg(g.rp + r + 1); }
+  int jcol[MERGE_K];
+  double av[MERGE_K];
+#pragma unroll
+  for (int i = 0; i < MERGE_K; ++i) {
+    jcol[i] = -1;
+    av[i] = 0.0;
+    if (i < k) {
+      jcol[i] = __ldg(A.col + a0 + i);
+      if (V) av[i] = __ldg(A.val + a0 + i);
+    }
+  }
+  int src[MERGE_K], len[MERGE_K];
+#pragma unroll
+  for (int i = 0; i < MERGE_K; ++i) {
+    src[i] = 0; len[i] = 0;
+    if (jcol[i] >= 0) {
+      src[i] = __ldg(B.rp + jcol[i]);
+      len[i] = __ldg(B.rp + jcol[i] + 1) - src[i];
+    }
+  }
+  int u = 0, nz = 0;
+#pragma unroll
+  for (int i = 0; i < MERGE_K; ++i) { u += len[i]; nz += len[i] > 0; }
+  int P, R;
+  const int pofs = warp_excl_scan(u, &P);
+  const int rofs = warp_excl_scan(nz, &R);
+  const int base = pofs + lane;            // this row's first staging slot
+  {
+    int d = 0, q = rofs;
+#pragma unroll
+    for (int i = 0; i < MERGE_K; ++i) {
+      if (len[i] > 0) {
+        r_run[q] = make_int2(src[i], ((pofs + d) << 8) | lane);
+        ++q;
+        d += len[i];
+      }
+    }
+  }
+  __syncwarp();
+
+  // 2. expand: asynchronous global -> shared copies of the tile's columns and values, all in flight
+  int e_cur = 0;
+  for (int cb = 0; cb < P; cb += 32) {
+    const int cand = e_cur + 1 + lane;
+    const int st = cand < R ? (r_run[cand].y >> 8) : KEY_NONE;
+    const unsigned off = (unsigned)(st - cb);
+    const unsigned bit = off < 32u ? (1u << off) : 0u;
+    const unsigned M = __reduce_or_sync(FULL, bit);
+    const int e = e_cur + __popc(M & lanemask_le());
+    const int p = cb + lane;
+    if (p < P) {
+      const int2 rr = r_run[e];
+      const int sp = rr.x + (p - (rr.y >> 8));
+      const int d = p + (rr.y & 31);      // product p of row t lives at slot p + t
+      cp_async4(s_col + d, B.col + sp);
+      if (V) cp_async8(s_val + d, B.val + sp);
+    }
+    e_cur = __shfl_sync(FULL, e, 31);
+  }
+  cp_async_wait_all();
+  __syncwarp();   // all copies landed; the run table is free
+
+  // 3. sort this lane's products by (column, run, index).  The run field is the rank of the
+  //    product's nonempty run: bits of `starts` mark where each nonempty run after the first begins.
+  unsigned key[N];
+  {
+    unsigned long long starts = 0;
+    int d = 0, q = 0;
+#pragma unroll
+    for (int i = 0; i < MERGE_K; ++i) {
+      if (len[i] > 0) {
+        if (d > 0) starts |= 1ull << d;
+        if (V) s_a[q * 32 + lane] = av[i];
+        ++q;
+      }
+      d += len[i];
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const unsigned rj = (unsigned)__popcll(starts & ((2ull << j) - 1ull));
+      key[j] = (j < u) ? ((s_col[base + j] << KB) | (rj << IB) | (unsigned)j) : PAD;
+    }
+  }
+  __syncwarp();   // every lane has its keys: s_col may now be overwritten
+  bitonic_sort<N>(key);
+
+  // 4. distinct columns
+  unsigned samemask_lo = 0, samemask_hi = 0;   // bit j: position j continues a group
+#pragma unroll
+  for (int j = 1; j < N; ++j) {
+    const bool same = (key[j] != PAD) && ((key[j] >> KB) == (key[j - 1] >> KB));
+    if (j < 32) samemask_lo |= same ? (1u << j) : 0u; else samemask_hi |= same ? (1u << (j - 32)) : 0u;
+  }
+  const int cnt = u - __popc(samemask_lo) - __popc(samemask_hi);
+  if (MODE == MODE_SYM) {
+    if (mine) g.rp[r] = cnt;
+    return;
+  }
+  // fused: the tile's entry count is known now; publish it before the reduce so the tiles
+  // after this one rarely wait for it
+  const int mycount = mine ? cnt : other;
+  int TA = 0;
+  const int oa = (MODE == MODE_FUSED) ? warp_excl_scan(mycount, &TA) : 0;
+  if (MODE == MODE_FUSED) tile_publish(g.tile_state, tile, TA);
+
+  // 5. reduce: acc = fma(a_rj, b_jx, acc) along each group in product order, the first product
+  //    added to +0.0 (the dense accumulator's start).  One FP64 instruction per sorted position,
+  //    issued only up to the longest row of the tile (the FP64 pipe costs a full warp slot even
+  //    for partial warps).  The group's sum goes to the slot of its last product (already read);
+  //    its key to output slot o of this lane's row.
+  const int umax = __reduce_max_sync(FULL, u);
+  {
+    int o = 0;
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      if (j < umax) {
+        const unsigned kj = key[j];
+        const bool valid = kj != PAD;
+        const int idx = (int)(kj & (unsigned)(N - 1));
+        const int run = (int)((kj >> IB) & 7u);
+        double a = 0.0, b = 0.0;
+        if (valid) {
+          b = s_val[base + idx];
+          a = s_a[run * 32 + lane];
+        }
+        const bool same = (j < 32) ? ((samemask_lo >> j) & 1u) : ((samemask_hi >> (j - 32)) & 1u);
+        acc = __fma_rn(a, b, same ? acc : 0.0);
+        bool next_same = false;
+        if (j + 1 < N) next_same = ((j + 1) < 32) ? ((samemask_lo >> (j + 1)) & 1u) : ((samemask_hi >> (j + 1 - 32)) & 1u);
+        if (valid && !next_same) {
+          s_col[base + o] = kj;
+          s_val[base + idx] = acc;
+          ++o;
+        }
+      }
+    }
+  }
+
+  // 6. place the tile in C
+  int TM;
+  const int om = warp_excl_scan(mine ? cnt : 0, &TM);   // this row's position in the tile's output list
+  long long gstart = 0;   // this row's first entry in C
+  int lim = INT_MAX;      // entries this row may write
+  if (MODE == MODE_NUM) {
+    gstart = gbeg;
+    lim = gend - gbeg;
+    if (mine && lim != cnt) atomicOr(&g.ctr->status, ST_MISMATCH);
+  } else {
+    const long long off = tile_lookback(g.tile_state, tile, TA, g.ctr);
+    gstart = off + oa;
+    if (inrange) {
+      if (gstart + mycount > INT_MAX) atomicOr(&g.ctr->status, ST_OVERFLOW);
+      g.rp[r] = (int)gstart;
+      if (r == A.rows - 1) {
+        g.rp[r + 1] = (int)(gstart + mycount);
+        g.ctr->nnzC = gstart + mycount;
+      }
+    }
+    if (off + TA > g.capacity) {
+      if (lane == 0) atomicOr(&g.ctr->status, ST_OVERFLOW);
+      return;
+    }
+  }
+  __syncwarp();
+
+  // 7. write the tile's entries: consecutive lanes on consecutive entries of C.
+  if (TM >= 24 * __popc(__ballot_sync(FULL, mine && cnt > 0))) {
+    // long rows: one row at a time
+    for (unsigned rows = __ballot_sync(FULL, mine && cnt > 0); rows; rows &= rows - 1) {
+      const int t = __ffs(rows) - 1;
+      const int ct = min(__shfl_sync(FULL, cnt, t), __shfl_sync(FULL, lim, t));
+      const int bt = __shfl_sync(FULL, base, t);
+      const long long gt = __shfl_sync(FULL, gstart, t);
+      for (int o = lane; o < ct; o += 32) {
+        const unsigned kf = s_col[bt + o];
+        const double vf = s_val[bt + (int)(kf & (unsigned)(N - 1))];
+        g.C_col[gt + o] = (int)(kf >> KB);
+        g.C_val[gt + o] = vf;
+      }
+    }
+  } else {
+    // short rows: entry f of the tile's list belongs to the last row t with om_t <= f (rows
+    // without entries share the start of the next row, so they are never chosen)
+    for (int cb = 0; cb < TM; cb += 32) {
+      const int f = cb + lane;
+      int t = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int cnd = t + step;
+        if (__shfl_sync(FULL, om, cnd) <= f) t = cnd;
+      }
+      const int o = f - __shfl_sync(FULL, om, t);
+      const int bt = __shfl_sync(FULL, base, t);
+      const long long gt = __shfl_sync(FULL, gstart, t);
+      const int lt = __shfl_sync(FULL, lim, t);
+      if (f < TM && o < lt) {
+        const unsigned kf = s_col[bt + o];
+        const double vf = s_val[bt + (int)(kf & (unsigned)(N - 1))];
+        g.C_col[gt + o] = (int)(kf >> KB);
+        g.C_val[gt + o] = vf;
+      }
+    }
+  }
+}
+
+template <int MODE, int N, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_merge(MergeArgs g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* wb = smem + (size_t)warp * SortSmem<MODE, N>::bytes;
+  const int ntiles = (g.A.rows + 31) >> 5;
+  if (MODE != MODE_FUSED) {
+    for (int tile = blockIdx.x * WARPS + warp; tile < ntiles; tile += gridDim.x * WARPS) {
+      merge_tile<MODE, N, WARPS>(g, tile, wb);
+      __syncwarp();
+    }
+  } else {
+    // Each warp takes its next tile from a ticket, so the tiles in flight are consecutive and
+    // every tile a look-back waits on is held by a warp that is already running.
+    while (true) {
+      int tile = 0;
+      if (lane == 0) tile = (int)atomicAdd(&g.ctr->ticket, 1u);
+      tile = __shfl_sync(FULL, tile, 0);
+      if (tile >= ntiles) break;
+      merge_tile<MODE, N, WARPS>(g, tile, wb);
+      __syncwarp();
+    }
+  }
+}
+
+template <int MODE, int N, int WARPS>
+static void launch_merge(const MergeArgs& g, cudaStream_t s) {
+  constexpr size_t bytes = (size_t)WARPS * SortSmem<MODE, N>::bytes;
+  auto kern = k_merge<MODE, N, WARPS>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  const int ntiles = (A.rows + 31) / 32;
+  const int ntiles = (g.A.rows + 31) / 32;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, bytes);
   if (per_sm < 1) per_sm = 1;
-  const int blocks = std::min((ntiles + WARPS - 1) / WARPS, num_sms() * per_sm * 8);
-  kern<<<blocks, WARPS * 32, bytes, s>>>(A, B, rowcls, cls, rp, counts, C_col, C_val, ctr);
+  int blocks;
+  if (MODE == MODE_FUSED) {
+    blocks = std::max(1, std::min((ntiles + WARPS - 1) / WARPS, num_sms() * per_sm));
+  } else {
+    blocks = std::max(1, std::min((ntiles + WARPS - 1) / WARPS, num_sms() * per_sm * 4));
+  }
+  kern<<<blocks, WARPS * 32, bytes, s>>>(g);
 }
 
-void launch_merge_symbolic(int cls, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* counts,
+int merge_max_cols() { return (1 << 23) - 2; }
+
+size_t fused_tile_state_bytes(int rows) { return (size_t)((rows + 31) / 32) * sizeof(unsigned long long); }
+
+void launch_merge_symbolic(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* counts,
                            Counters* ctr, cudaStream_t s) {
-  if (cls == CLS_M1) launch_merge<false, 1024, 8>(A, B, rowcls, cls, nullptr, counts, nullptr, nullptr, ctr, s);
-  else launch_merge<false, 2048, 8>(A, B, rowcls, cls, nullptr, counts, nullptr, nullptr, ctr, s);
+  MergeArgs g{A, B, rowcls, counts, nullptr, nullptr, 0, nullptr, ctr};
+  if (!wide) launch_merge<MODE_SYM, 32, 4>(g, s);
+  else launch_merge<MODE_SYM, 64, 4>(g, s);
 }
 
-void launch_merge_numeric(int cls, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, const int* rp,
+void launch_merge_numeric(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, const int* rp,
                           int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
-  if (cls == CLS_M1) launch_merge<true, 1024, 4>(A, B, rowcls, cls, rp, nullptr, C_col, C_val, ctr, s);
-  else launch_merge<true, 2048, 4>(A, B, rowcls, cls, rp, nullptr, C_col, C_val, ctr, s);
+  MergeArgs g{A, B, rowcls, const_cast<int*>(rp), C_col, C_val, 0, nullptr, ctr};
+  if (!wide) launch_merge<MODE_NUM, 32, 1>(g, s);
+  else launch_merge<MODE_NUM, 64, 1>(g, s);
+}
+
+void launch_merge_fused(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* rp, int* C_col,
+                        double* C_val, long long capacity, unsigned long long* tile_state, Counters* ctr,
+                        cudaStream_t s) {
+  MergeArgs g{A, B, rowcls, rp, C_col, C_val, capacity, tile_state, ctr};
+  if (!wide) launch_merge<MODE_FUSED, 32, 1>(g, s);
+  else launch_merge<MODE_FUSED, 64, 1>(g, s);
 }
 
 }  // namespace spg

@@ -19,7 +19,7 @@ int num_sms() {
 // of row r (Section III); summed over rows it is the never-underestimating nnz
 // estimate of Section IV-B.  Each row gets the class of accumulator it will use.
 // ---------------------------------------------------------------------------
-constexpr int BIN_THREADS = 256;
+constexpr int BIN_THREADS = 1024;
 
 __global__ void __launch_bounds__(BIN_THREADS)
 k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l1, int* l2, int* l3, int* l4,
@@ -34,12 +34,28 @@ k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l
     const int a0 = A.rp[r], a1 = A.rp[r + 1];
     const int k = a1 - a0;
     if (k < 0) bad = true;
-    for (int p = a0; p < a1; ++p) {
-      const int j = __ldg(A.col + p);
-      if ((unsigned)j >= (unsigned)B.rows) { bad = true; continue; }
-      const int len = __ldg(B.rp + j + 1) - __ldg(B.rp + j);
-      if (len < 0) { bad = true; continue; }
-      u += len;
+    // eight entries per round, all loads of a round in flight together
+    for (int p0 = a0; p0 < a1; p0 += 8) {
+      int j[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) j[i] = (p0 + i < a1) ? __ldg(A.col + p0 + i) : -1;
+      int lo[8], hi[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        lo[i] = hi[i] = 0;
+        if (j[i] >= 0) {
+          if ((unsigned)j[i] >= (unsigned)B.rows) { bad = true; continue; }
+          lo[i] = __ldg(B.rp + j[i]);
+          hi[i] = __ldg(B.rp + j[i] + 1);
+        } else if (p0 + i < a1) {
+          bad = true;   // negative column index
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int len = hi[i] - lo[i];
+        if (len < 0) bad = true; else u += len;
+      }
     }
     if (k <= lim.merge_k && u <= lim.m1_u) c = CLS_M1;
     else if (k <= lim.merge_k && u <= lim.m2_u) c = CLS_M2;
@@ -48,25 +64,34 @@ k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l
     else c = CLS_G;
     cls[r] = (uint8_t)c;
   }
-  // warp-aggregated appends to the class lists (order within a warp preserved)
+  // warp-aggregated appends to the class lists (rare classes), block-aggregated counts
+  __shared__ int s_cnt[NUM_CLS];
+  __shared__ long long s_sum[BIN_THREADS / 32];
+  __shared__ long long s_max[BIN_THREADS / 32];
+  if (threadIdx.x < NUM_CLS) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
 #pragma unroll
   for (int q = 0; q < NUM_CLS; ++q) {
     const unsigned mask = __ballot_sync(FULL, c == q);
     if (mask) {
-      const int leader = __ffs(mask) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(&ctr->count[q], __popc(mask));
-      base = __shfl_sync(FULL, base, leader);
-      if (c == q && lists[q]) lists[q][base + __popc(mask & lanemask_lt())] = r;
+      if (lists[q]) {
+        const int leader = __ffs(mask) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&ctr->count[q], __popc(mask));
+        base = __shfl_sync(FULL, base, leader);
+        if (c == q) lists[q][base + __popc(mask & lanemask_lt())] = r;
+      } else if (lane == 0) {
+        atomicAdd(&s_cnt[q], __popc(mask));
+      }
     }
   }
-  // block totals: F and the largest row
-  __shared__ long long s_sum[BIN_THREADS / 32];
-  __shared__ long long s_max[BIN_THREADS / 32];
+  // block totals: F, the largest row, the largest merge-class row
   long long ws = warp_sum_ll(u);
   long long wm = u;
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) wm = max(wm, __shfl_xor_sync(FULL, wm, d));
+  const int um = __reduce_max_sync(FULL, (c == CLS_M1 || c == CLS_M2) ? (int)u : 0);
+  if (lane == 0 && um > 0) atomicMax(&ctr->max_u_merge, um);
   const bool anybad = __any_sync(FULL, bad);
   if (lane == 0) {
     s_sum[threadIdx.x >> 5] = ws;
@@ -74,6 +99,7 @@ k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l
     if (anybad) atomicOr(&ctr->status, ST_INVALID);
   }
   __syncthreads();
+  if (threadIdx.x < NUM_CLS && s_cnt[threadIdx.x]) atomicAdd(&ctr->count[threadIdx.x], s_cnt[threadIdx.x]);
   if (threadIdx.x == 0) {
     long long t = 0, mx = 0;
     for (int w = 0; w < BIN_THREADS / 32; ++w) { t += s_sum[w]; mx = max(mx, s_max[w]); }
@@ -83,9 +109,11 @@ k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l
   }
 }
 
-void launch_bin(const DevCsr& A, const DevCsr& B, const Limits& lim, uint8_t* cls, int* const lists[NUM_CLS],
+void launch_bin(const DevCsr& A, const DevCsr& B, const Limits& lim_in, uint8_t* cls, int* const lists[NUM_CLS],
                 Counters* ctr, cudaStream_t s) {
   if (A.rows <= 0) return;
+  Limits lim = lim_in;
+  if (B.cols > merge_max_cols()) { lim.m1_u = -1; lim.m2_u = -1; }   // sort keys hold column << log2(N)
   const int grid = (A.rows + BIN_THREADS - 1) / BIN_THREADS;
   k_bin<<<grid, BIN_THREADS, 0, s>>>(A, B, lim, cls, lists[0], lists[1], lists[2], lists[3], lists[4], ctr);
 }

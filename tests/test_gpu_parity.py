@@ -12,44 +12,51 @@ from tests.gpu_util import compare, gpu_product
 
 pytestmark = pytest.mark.gpu
 
+PATHS = pytest.mark.parametrize("fused", [False, True], ids=["3call", "fused"])
+
 
 def opts(**kw):
     from paper_1303_1651_gb300 import binding
     return binding.options(**kw)
 
 
-def test_laplacian_64_squared():
+@PATHS
+def test_laplacian_64_squared(fused):
     A = synth.laplacian5(64)
-    C = gpu_product(A, A)
+    C = gpu_product(A, A, fused=fused)
     R = oracle.spgemm(A, A)
     compare(C, R, exact=True)
     assert C["info"]["products"] == 100104 and C["nnz"] == 51972
 
 
-def test_random_4096_k8():
+@PATHS
+def test_random_4096_k8(fused):
     A, B = synth.random_k(4096, 8, synth.SEED_A), synth.random_k(4096, 8, synth.SEED_B)
-    compare(gpu_product(A, B), oracle.spgemm(A, B), exact=True)
+    compare(gpu_product(A, B, fused=fused), oracle.spgemm(A, B), single=True)
 
 
+@PATHS
 @pytest.mark.parametrize("k", [1, 2, 4, 5, 7, 8])
-def test_random_merge_classes(k):
+def test_random_merge_classes(k, fused):
     A, B = synth.random_k(3000, k, 11 + k), synth.random_k(3000, k, 31 + k)
-    C = gpu_product(A, B)
-    compare(C, oracle.spgemm(A, B), exact=True)
+    C = gpu_product(A, B, fused=fused)
+    compare(C, oracle.spgemm(A, B), single=True)
 
 
+@PATHS
 @pytest.mark.parametrize("k", [9, 16, 32])
-def test_random_hash_classes(k):
+def test_random_hash_classes(k, fused):
     A, B = synth.random_k(2000, k, 5 + k), synth.random_k(2000, k, 7 + k)
-    C = gpu_product(A, B)
+    C = gpu_product(A, B, fused=fused)
     compare(C, oracle.spgemm(A, B))
     assert C["info"]["rows_per_class"]["W"] + C["info"]["rows_per_class"]["B"] > 0
 
 
-def test_power_law_all_classes():
+@PATHS
+def test_power_law_all_classes(fused):
     A = synth.power_law(3000, 3000, 3, alpha=1.5, max_len=3000)
     B = synth.power_law(3000, 4000, 4, alpha=1.5, max_len=400)
-    C = gpu_product(A, B)
+    C = gpu_product(A, B, fused=fused)
     R = oracle.spgemm(A, B)
     compare(C, R)
     cls = C["info"]["rows_per_class"]
@@ -62,20 +69,23 @@ def test_power_law_all_classes():
     dict(m1_max_u=-1, m2_max_u=-1, warp_max_u=-1, block_max_u=-1),   # dense fallback only
     dict(m1_max_u=4, m2_max_u=16, warp_max_u=40, block_max_u=100, dense_slabs=3),
 ])
-def test_forced_classes(forced):
+@PATHS
+def test_forced_classes(forced, fused):
     A = synth.power_law(1500, 1200, 8, alpha=1.7, max_len=300)
     B = synth.power_law(1200, 900, 9, alpha=1.7, max_len=100)
-    compare(gpu_product(A, B, opts(**forced)), oracle.spgemm(A, B))
+    compare(gpu_product(A, B, opts(**forced), fused=fused), oracle.spgemm(A, B))
 
 
-def test_laplacian_forced_classes_exact():
+@PATHS
+def test_laplacian_forced_classes_exact(fused):
     A = synth.laplacian5(40)
     R = oracle.spgemm(A, A)
     for forced in (dict(m1_max_u=-1, m2_max_u=-1), dict(m1_max_u=-1, m2_max_u=-1, warp_max_u=-1, block_max_u=-1)):
-        compare(gpu_product(A, A, opts(**forced)), R, exact=True)   # small integers: every order is exact
+        compare(gpu_product(A, A, opts(**forced), fused=fused), R, exact=True)   # small integers: every order is exact
 
 
-def test_rectangular_and_empty_rows():
+@PATHS
+def test_rectangular_and_empty_rows(fused):
     rng = np.random.default_rng(12)
     lengths = rng.integers(0, 20, size=700)
     lengths[100:200] = 0                        # a block of empty rows
@@ -83,52 +93,58 @@ def test_rectangular_and_empty_rows():
     blen = rng.integers(0, 25, size=300)
     blen[::7] = 0                               # empty rows of B as well
     B = synth.random_lengths(blen, 1100, 13)    # 300 x 1100
-    compare(gpu_product(A, B), oracle.spgemm(A, B))
+    compare(gpu_product(A, B, fused=fused), oracle.spgemm(A, B))
 
 
-def test_degenerate_shapes():
+@PATHS
+def test_degenerate_shapes(fused):
     one = synth.from_dense(np.array([[2.5]]))
-    C = gpu_product(one, one)
+    C = gpu_product(one, one, fused=fused)
     assert list(C["val"]) == [6.25]
     Z = synth.CSR(0, 5, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
     B = synth.random_k(5, 2, 1)
-    C = gpu_product(Z, B)
+    C = gpu_product(Z, B, fused=fused)
     assert C["nnz"] == 0 and list(C["row_ptr"]) == [0]
     E = synth.CSR(4, 5, np.zeros(5, np.int32), np.zeros(0, np.int32), np.zeros(0))
-    C = gpu_product(E, B)
+    C = gpu_product(E, B, fused=fused)
     assert C["nnz"] == 0 and list(C["row_ptr"]) == [0] * 5
     Bz = synth.CSR(5, 3, np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0))
     A = synth.random_k(7, 2, 3, ncols=5)
-    C = gpu_product(A, Bz)      # every B row empty
+    C = gpu_product(A, Bz, fused=fused)      # every B row empty
     assert C["nnz"] == 0
 
 
-def test_cancellation_and_explicit_zeros():
+@PATHS
+def test_cancellation_and_explicit_zeros(fused):
     A = synth.CSR(1, 2, np.array([0, 2], np.int32), np.array([0, 1], np.int32), np.array([1.0, 1.0]))
     B = synth.CSR(2, 1, np.array([0, 1, 2], np.int32), np.array([0, 0], np.int32), np.array([1.0, -1.0]))
-    C = gpu_product(A, B)
+    C = gpu_product(A, B, fused=fused)
     assert C["nnz"] == 1 and C["val"][0] == 0.0
     Az = synth.random_k(500, 6, 3)
     Az.val[::3] = 0.0
     Bz = synth.random_k(500, 6, 4)
     Bz.val[::5] = 0.0
-    compare(gpu_product(Az, Bz), oracle.spgemm(Az, Bz), exact=True)
+    compare(gpu_product(Az, Bz, fused=fused), oracle.spgemm(Az, Bz), single=True)
 
 
-def test_unsorted_A_and_duplicates_in_A():
+@PATHS
+def test_unsorted_A_and_duplicates_in_A(fused):
     A = synth.duplicate_entries(synth.random_k(800, 5, 21), 22)   # unsorted rows with repeated columns
     B = synth.random_k(800, 6, 23)
-    compare(gpu_product(A, B), oracle.spgemm(A, B))
+    compare(gpu_product(A, B, fused=fused), oracle.spgemm(A, B))
 
 
-def test_unsorted_B_reported_for_merge_rows_and_hashed_otherwise():
-    from paper_1303_1651_gb300 import binding
+@PATHS
+def test_unsorted_and_duplicate_B_rows(fused):
+    # the merge classes sort every product, so B's rows may be in any order and repeat columns
     A = synth.random_k(600, 4, 31)
     B = synth.shuffle_rows(synth.random_k(600, 6, 32), 33)
-    with pytest.raises(binding.SpgemmError) as e:
-        gpu_product(A, B)
-    assert e.value.name == "SPGEMM_ERR_UNSORTED"
-    compare(gpu_product(A, B, opts(m1_max_u=-1, m2_max_u=-1)), oracle.spgemm(A, B))
+    R = oracle.spgemm(A, B)
+    compare(gpu_product(A, B, fused=fused), R, single=True)
+    compare(gpu_product(A, B, opts(m1_max_u=-1, m2_max_u=-1), fused=fused), R)
+    Bd = synth.duplicate_entries(synth.random_k(600, 5, 34), 35)
+    compare(gpu_product(A, Bd, fused=fused), oracle.spgemm(A, Bd), single=True)
+    compare(gpu_product(A, Bd, opts(m1_max_u=-1, m2_max_u=-1), fused=fused), oracle.spgemm(A, Bd))
 
 
 def test_numeric_repeatable_with_new_values():
@@ -144,7 +160,7 @@ def test_numeric_repeatable_with_new_values():
             C = prod.numeric(A_val=torch.from_numpy(A2.val).cuda())
             binding.spgemm_status(prod.plan)
             out = C.to_host()
-            compare(out, oracle.spgemm(A2, B), exact=True)
+            compare(out, oracle.spgemm(A2, B), single=True)
     finally:
         prod.close()
 
@@ -157,3 +173,54 @@ def test_validate_option_flags_bad_columns():
     with pytest.raises(binding.SpgemmError) as e:
         gpu_product(A, B, opts(validate=1))
     assert e.value.name == "SPGEMM_ERR_INVALID"
+
+
+def test_fused_capacity_too_small_reported():
+    import torch
+    from paper_1303_1651_gb300 import binding
+    A = synth.random_k(3000, 6, 61)
+    B = synth.random_k(3000, 6, 62)
+    dA, dB = binding.DeviceCSR.from_host(A), binding.DeviceCSR.from_host(B)
+    ws = torch.empty(binding.spgemm_workspace_size(dA, dB), dtype=torch.uint8, device="cuda")
+    plan = binding.spgemm_plan(dA, dB, ws)
+    try:
+        C_rp = torch.empty(A.rows + 1, dtype=torch.int32, device="cuda")
+        cap = 1000
+        C_col = torch.full((cap + 64,), -7, dtype=torch.int32, device="cuda")
+        C_val = torch.zeros(cap + 64, dtype=torch.float64, device="cuda")
+        with pytest.raises(binding.SpgemmError) as e:
+            binding.spgemm_compute(plan, dA.val, dB.val, C_rp, C_col[:cap], C_val[:cap])
+        assert e.value.name == "SPGEMM_ERR_OVERFLOW"
+        assert bool((C_col[cap:] == -7).all())      # nothing written past the capacity
+    finally:
+        binding.spgemm_free(plan)
+
+
+def test_fused_then_numeric_with_new_values():
+    import torch
+    from paper_1303_1651_gb300 import binding
+    A = synth.random_k(5000, 7, 71)
+    B = synth.laplacian5(70)
+    A = synth.random_k(4900, 7, 71)
+    dA, dB = binding.DeviceCSR.from_host(A), binding.DeviceCSR.from_host(B)
+    ws = torch.empty(binding.spgemm_workspace_size(dA, dB), dtype=torch.uint8, device="cuda")
+    plan = binding.spgemm_plan(dA, dB, ws)
+    try:
+        F = binding.spgemm_plan_info(plan)["products"]
+        C_rp = torch.empty(A.rows + 1, dtype=torch.int32, device="cuda")
+        C_col = torch.empty(F, dtype=torch.int32, device="cuda")
+        C_val = torch.empty(F, dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        binding.spgemm_plan_set_events(plan, e0, e1)
+        nnz = binding.spgemm_compute(plan, dA.val, dB.val, C_rp, C_col, C_val)
+        assert e0.elapsed_time(e1) > 0
+        R = oracle.spgemm(A, B)
+        got = dict(row_ptr=C_rp.cpu().numpy(), col_idx=C_col[:nnz].cpu().numpy(), val=C_val[:nnz].cpu().numpy())
+        compare(got, R, single=True)
+        A2 = A.copy(); A2.val = -2.0 * A.val
+        binding.spgemm_numeric(plan, torch.from_numpy(A2.val).cuda(), dB.val, C_col, C_val)
+        binding.spgemm_status(plan)
+        got = dict(row_ptr=C_rp.cpu().numpy(), col_idx=C_col[:nnz].cpu().numpy(), val=C_val[:nnz].cpu().numpy())
+        compare(got, oracle.spgemm(A2, B), single=True)
+    finally:
+        binding.spgemm_free(plan)

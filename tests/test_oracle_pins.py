@@ -65,6 +65,24 @@ def test_flop_formula_matches_row_counts():
         pins.check_csr_invariants(C)
 
 
+def test_entry_product_counts():
+    # every multiplication lands in exactly one entry; the Laplacian^2 diagonal gathers 1 + deg products
+    A = synth.power_law(200, 150, 31, max_len=30)
+    B = synth.power_law(150, 170, 32, max_len=20)
+    C = oracle.spgemm(A, B)
+    assert int(C["count"].sum()) == C["F"] and C["count"].min(initial=1) >= 1
+    n = 6
+    L = synth.laplacian5(n)
+    C = oracle.spgemm(L, L)
+    for i in range(n):
+        for j in range(n):
+            r = i * n + j
+            seg = slice(C["row_ptr"][r], C["row_ptr"][r + 1])
+            diag = np.nonzero(C["col_idx"][seg] == r)[0][0]
+            deg = (i > 0) + (i < n - 1) + (j > 0) + (j < n - 1)
+            assert C["count"][seg][diag] == 1 + deg
+
+
 def test_row_counts_are_products_per_row():
     A = synth.random_k(500, 6, 1)
     B = synth.power_law(500, 400, 2, max_len=30)
