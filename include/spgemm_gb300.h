@@ -162,6 +162,36 @@ spgemm_status_t spgemm_numeric(spgemm_plan_t plan, const double* A_val, const do
 spgemm_status_t spgemm_compute(spgemm_plan_t plan, const double* A_val, const double* B_val, int32_t* C_row_ptr,
                                int32_t* C_col, double* C_val, int64_t capacity, int64_t* nnz_c, void* stream);
 
+/* spgemm_compute without the host synchronisation, for CUDA-graph capture and for batches: the
+ * work is only enqueued on stream.  nnz(C) lands in C_row_ptr[A.rows] and, if nnz_c_device is not
+ * NULL, as an int64 in device memory at nnz_c_device.  Device errors are read by spgemm_status.
+ * Capture it after spgemm_plan (which synchronises) and replay the graph as long as A's and B's
+ * structures and the buffers stay the same; values may change between replays.  A batch of
+ * independent products runs as one call on the block-diagonal matrices diag(A_1..A_P) and
+ * diag(B_1..B_P): each problem's rows only reach its own block of B.
+ * Errors: STATE, INVALID, CUDA. */
+spgemm_status_t spgemm_compute_async(spgemm_plan_t plan, const double* A_val, const double* B_val,
+                                     int32_t* C_row_ptr, int32_t* C_col, double* C_val, int64_t capacity,
+                                     int64_t* nnz_c_device, void* stream);
+
+/* Bytes of device workspace spgemm_backward needs to form dB: the transpose of A's structure (the
+ * CSR -> CSC conversion of Section IV-A).  Errors: INVALID. */
+spgemm_status_t spgemm_backward_workspace_size(const spgemm_csr_t* A, const spgemm_csr_t* B, size_t* bytes);
+
+/* Gradients of a loss L through C = A * B, given dC = dL/dC on C's structure (aligned with C_col):
+ *   dA_ij = sum_x B_jx dC_ix  for every entry (i, j) of A   (aligned with A's entries),
+ *   dB_jx = sum_i A_ij dC_ix  for every entry (j, x) of B   (aligned with B's entries).
+ * Needs the plan after spgemm_compute / spgemm_numeric (C's structure).  dA_val or dB_val may be
+ * NULL to skip it; B_val is read for dA and A_val for dB.  workspace (device, 256-byte aligned, at
+ * least spgemm_backward_workspace_size bytes) is needed only for dB; the transpose built in it is
+ * kept and reused while the same workspace is passed.  Each entry accumulates its terms in
+ * storage order with fused multiply-adds.  Enqueues on stream; no synchronisation.
+ * Errors: STATE, INVALID, ALLOC, CUDA; a term missing from C's structure sets SPGEMM_ERR_MISMATCH
+ * (read by spgemm_status). */
+spgemm_status_t spgemm_backward(spgemm_plan_t plan, const double* A_val, const double* B_val, const double* dC_val,
+                                double* dA_val, double* dB_val, void* workspace, size_t workspace_bytes,
+                                void* stream);
+
 /* Synchronise stream and report the plan's sticky device status (OK or the first error). */
 spgemm_status_t spgemm_status(spgemm_plan_t plan, void* stream);
 

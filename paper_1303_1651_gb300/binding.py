@@ -72,6 +72,9 @@ def load():
         lib.spgemm_compute.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int64, P(ctypes.c_int64), vp]
         lib.spgemm_status.argtypes = [vp, vp]
         lib.spgemm_plan_set_events.argtypes = [vp, vp, vp]
+        lib.spgemm_compute_async.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp, vp]
+        lib.spgemm_backward_workspace_size.argtypes = [P(spgemm_csr_t), P(spgemm_csr_t), P(ctypes.c_size_t)]
+        lib.spgemm_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         lib.spgemm_plan_info.argtypes = [vp, P(spgemm_info_t)]
         lib.spgemm_free.argtypes = [vp]
         lib.spgemm_error_string.argtypes = [ctypes.c_int]
@@ -79,7 +82,8 @@ def load():
         lib.spgemm_version.restype = ctypes.c_int32
         for name in ("spgemm_workspace_size", "spgemm_plan", "spgemm_symbolic", "spgemm_numeric",
                      "spgemm_compute", "spgemm_status", "spgemm_plan_info", "spgemm_free",
-                     "spgemm_plan_set_events"):
+                     "spgemm_plan_set_events", "spgemm_compute_async", "spgemm_backward_workspace_size",
+                     "spgemm_backward"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -183,6 +187,30 @@ def spgemm_compute(plan: int, A_val: torch.Tensor, B_val: torch.Tensor, C_row_pt
     _check(load().spgemm_compute(plan, _ptr(A_val), _ptr(B_val), C_row_ptr.data_ptr(), _ptr(C_col), _ptr(C_val),
                                  cap, ctypes.byref(nnz), _stream(stream)), "spgemm_compute")
     return int(nnz.value)
+
+
+def spgemm_compute_async(plan: int, A_val: torch.Tensor, B_val: torch.Tensor, C_row_ptr: torch.Tensor,
+                         C_col: torch.Tensor, C_val: torch.Tensor, nnz_device: torch.Tensor | None = None,
+                         stream=None):
+    """Enqueue the single-pass product without synchronising (CUDA-graph capturable)."""
+    cap = min(C_col.numel(), C_val.numel())
+    _check(load().spgemm_compute_async(plan, _ptr(A_val), _ptr(B_val), C_row_ptr.data_ptr(), _ptr(C_col),
+                                       _ptr(C_val), cap, _ptr(nnz_device), _stream(stream)), "spgemm_compute_async")
+
+
+def spgemm_backward_workspace_size(A: DeviceCSR, B: DeviceCSR) -> int:
+    n = ctypes.c_size_t(0)
+    a, b = A.desc(False), B.desc(False)
+    _check(load().spgemm_backward_workspace_size(ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
+           "spgemm_backward_workspace_size")
+    return int(n.value)
+
+
+def spgemm_backward(plan: int, A_val, B_val, dC_val, dA_val=None, dB_val=None, workspace=None, stream=None):
+    """dA = (dC B^T) on A's structure and dB = (A^T dC) on B's structure (either may be None)."""
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(load().spgemm_backward(plan, _ptr(A_val), _ptr(B_val), _ptr(dC_val), _ptr(dA_val), _ptr(dB_val),
+                                  _ptr(workspace), ws_bytes, _stream(stream)), "spgemm_backward")
 
 
 def spgemm_status(plan: int, stream=None):

@@ -98,7 +98,9 @@ struct spgemm_plan_s {
   Counters h{};                 // host copy of the counters after the last synchronising call
   int state = 0;                // 1 planned, 2 symbolic done
   int32_t* C_rp = nullptr;
+  int32_t* C_col = nullptr;     // set by numeric / compute (the backward reads C's structure)
   bool slabs_clean = false;
+  const void* transposed_ws = nullptr;   // backward workspace holding A's transpose, once built
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // optional, recorded around the compute kernels
 };
 
@@ -196,7 +198,7 @@ spgemm_status_t spgemm_symbolic(spgemm_plan_t p, int32_t* C_row_ptr, int64_t* nn
   if (cnt[CLS_G] > 0)
     launch_dense_symbolic(p->A, p->B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs,
                           C_row_ptr, p->ctr, s);
-  launch_scan(C_row_ptr, (long long)m + 1, (unsigned long long*)(p->ws + L.scan), p->ctr, s);
+  launch_scan(C_row_ptr, (long long)m + 1, (unsigned long long*)(p->ws + L.scan), p->ctr, &p->ctr->nnzC, s);
   cudaMemcpyAsync(&p->h, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
   const spgemm_status_t st = status_from_bits(p->h.status);
@@ -231,16 +233,16 @@ spgemm_status_t spgemm_numeric(spgemm_plan_t p, const double* A_val, const doubl
                          C_col, C_val, p->ctr, s);
   if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
   if (cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  p->C_col = C_col;
   return SPGEMM_OK;
 }
 
-spgemm_status_t spgemm_compute(spgemm_plan_t p, const double* A_val, const double* B_val, int32_t* C_row_ptr,
-                               int32_t* C_col, double* C_val, int64_t capacity, int64_t* nnz_c, void* stream) {
+static spgemm_status_t compute_enqueue(spgemm_plan_t p, const double* A_val, const double* B_val, int32_t* C_row_ptr,
+                                       int32_t* C_col, double* C_val, int64_t capacity, cudaStream_t s) {
   if (!p || p->state < 1) return SPGEMM_ERR_STATE;
-  if (!C_row_ptr || !nnz_c || capacity < 0) return SPGEMM_ERR_INVALID;
+  if (!C_row_ptr || capacity < 0) return SPGEMM_ERR_INVALID;
   if ((!A_val && p->A.nnz > 0) || (!B_val && p->B.nnz > 0)) return SPGEMM_ERR_INVALID;
   if ((!C_col || !C_val) && capacity > 0) return SPGEMM_ERR_INVALID;
-  cudaStream_t s = (cudaStream_t)stream;
   const Layout& L = p->L;
   const int m = p->A.rows;
   DevCsr A = p->A, B = p->B;
@@ -248,48 +250,101 @@ spgemm_status_t spgemm_compute(spgemm_plan_t p, const double* A_val, const doubl
   B.val = B_val;
   if (m == 0) {
     cudaMemsetAsync(C_row_ptr, 0, sizeof(int32_t), s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return SPGEMM_ERR_CUDA;
-    *nnz_c = 0;
-    p->C_rp = C_row_ptr;
-    p->h.nnzC = 0;
-    p->state = 2;
-    return SPGEMM_OK;
+    cudaMemsetAsync(&p->ctr->nnzC, 0, sizeof(long long), s);
+  } else {
+    const int* cnt = p->h.count;
+    uint8_t* cls = p->ws + L.cls;
+    cudaMemsetAsync(&p->ctr->ticket, 0, sizeof(unsigned), s);
+    cudaMemsetAsync(p->ws + L.fused, 0, fused_tile_state_bytes(m), s);
+    // rows of the hash and dense classes: counts first (the fused pass places every row)
+    if (cnt[CLS_G] > 0 && !p->slabs_clean) {
+      cudaMemsetAsync(p->ws + L.slabs, 0, (size_t)p->nslabs * dense_slab_bytes(p->B.cols), s);
+      p->slabs_clean = true;
+    }
+    if (p->ev_start) cudaEventRecord(p->ev_start, s);
+    if (cnt[CLS_W] > 0)
+      launch_hash_symbolic(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s);
+    if (cnt[CLS_B] > 0)
+      launch_hash_symbolic(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s);
+    if (cnt[CLS_G] > 0)
+      launch_dense_symbolic(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs,
+                            C_row_ptr, p->ctr, s);
+    const int wide = p->h.max_u_merge > 32;
+    launch_merge_fused(wide, A, B, cls, C_row_ptr, C_col, C_val, capacity,
+                       (unsigned long long*)(p->ws + L.fused), p->ctr, s);
+    if (cnt[CLS_W] > 0)
+      launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, C_col, C_val, p->ctr, s);
+    if (cnt[CLS_B] > 0)
+      launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, C_col, C_val, p->ctr, s);
+    if (cnt[CLS_G] > 0)
+      launch_dense_numeric(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs, C_row_ptr,
+                           C_col, C_val, p->ctr, s);
+    if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
   }
-  const int* cnt = p->h.count;
-  uint8_t* cls = p->ws + L.cls;
-  cudaMemsetAsync(&p->ctr->ticket, 0, sizeof(unsigned), s);
-  cudaMemsetAsync(p->ws + L.fused, 0, fused_tile_state_bytes(m), s);
-  // rows of the hash and dense classes: counts first (the fused pass places every row)
-  if (cnt[CLS_G] > 0 && !p->slabs_clean) {
-    cudaMemsetAsync(p->ws + L.slabs, 0, (size_t)p->nslabs * dense_slab_bytes(p->B.cols), s);
-    p->slabs_clean = true;
-  }
-  if (p->ev_start) cudaEventRecord(p->ev_start, s);
-  if (cnt[CLS_W] > 0)
-    launch_hash_symbolic(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s);
-  if (cnt[CLS_B] > 0)
-    launch_hash_symbolic(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s);
-  if (cnt[CLS_G] > 0)
-    launch_dense_symbolic(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs,
-                          C_row_ptr, p->ctr, s);
-  const int wide = p->h.max_u_merge > 32;
-  launch_merge_fused(wide, A, B, cls, C_row_ptr, C_col, C_val, capacity,
-                     (unsigned long long*)(p->ws + L.fused), p->ctr, s);
-  if (cnt[CLS_W] > 0)
-    launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, C_col, C_val, p->ctr, s);
-  if (cnt[CLS_B] > 0)
-    launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, C_col, C_val, p->ctr, s);
-  if (cnt[CLS_G] > 0)
-    launch_dense_numeric(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs, C_row_ptr,
-                         C_col, C_val, p->ctr, s);
-  if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
+  if (cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  p->C_rp = C_row_ptr;
+  p->C_col = C_col;
+  p->state = 2;
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_compute(spgemm_plan_t p, const double* A_val, const double* B_val, int32_t* C_row_ptr,
+                               int32_t* C_col, double* C_val, int64_t capacity, int64_t* nnz_c, void* stream) {
+  if (!nnz_c) return SPGEMM_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const spgemm_status_t e = compute_enqueue(p, A_val, B_val, C_row_ptr, C_col, C_val, capacity, s);
+  if (e != SPGEMM_OK) return e;
   cudaMemcpyAsync(&p->h, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
   const spgemm_status_t st = status_from_bits(p->h.status);
   if (st != SPGEMM_OK) return st;
-  p->C_rp = C_row_ptr;
-  p->state = 2;
   *nnz_c = p->h.nnzC;
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_compute_async(spgemm_plan_t p, const double* A_val, const double* B_val, int32_t* C_row_ptr,
+                                     int32_t* C_col, double* C_val, int64_t capacity, int64_t* nnz_c_device,
+                                     void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const spgemm_status_t e = compute_enqueue(p, A_val, B_val, C_row_ptr, C_col, C_val, capacity, s);
+  if (e != SPGEMM_OK) return e;
+  if (nnz_c_device) cudaMemcpyAsync(nnz_c_device, &p->ctr->nnzC, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  if (cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_backward_workspace_size(const spgemm_csr_t* A, const spgemm_csr_t* B, size_t* bytes) {
+  if (!bytes || !desc_ok(A) || !desc_ok(B) || A->cols != B->rows) return SPGEMM_ERR_INVALID;
+  *bytes = transpose_bytes(A->cols, A->nnz);
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_backward(spgemm_plan_t p, const double* A_val, const double* B_val, const double* dC_val,
+                                double* dA_val, double* dB_val, void* workspace, size_t workspace_bytes,
+                                void* stream) {
+  if (!p || p->state < 2 || !p->C_rp || (!p->C_col && p->h.nnzC > 0)) return SPGEMM_ERR_STATE;
+  if (!dC_val && p->h.nnzC > 0) return SPGEMM_ERR_INVALID;
+  if (dA_val && !B_val && p->B.nnz > 0) return SPGEMM_ERR_INVALID;
+  if (dB_val) {
+    if (!A_val && p->A.nnz > 0) return SPGEMM_ERR_INVALID;
+    if (!workspace || workspace_bytes < transpose_bytes(p->A.cols, p->A.nnz) || ((uintptr_t)workspace % ALIGN) != 0)
+      return SPGEMM_ERR_ALLOC;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  DevCsr A = p->A, B = p->B;
+  A.val = A_val;
+  B.val = B_val;
+  if (p->ev_start) cudaEventRecord(p->ev_start, s);
+  if (dA_val) launch_grad_a(A, B, p->C_rp, p->C_col, dC_val, dA_val, p->ctr, s);
+  if (dB_val) {
+    if (p->transposed_ws != workspace) {
+      launch_transpose(A, workspace, p->ctr, s);
+      p->transposed_ws = workspace;
+    }
+    launch_grad_b(A, B, workspace, p->C_rp, p->C_col, dC_val, dB_val, p->ctr, s);
+  }
+  if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
+  if (cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
   return SPGEMM_OK;
 }
 

@@ -12,7 +12,9 @@ void launch_bin(const DevCsr& A, const DevCsr& B, const Limits& lim, uint8_t* cl
 
 // a3: exclusive scan, in place, of counts[0..n-2] into row_ptr[0..n-1] (n = rows + 1).
 size_t scan_tile_state_bytes(long long n);
-void launch_scan(int* rp, long long n, unsigned long long* tile_state, Counters* ctr, cudaStream_t s);
+// The total (rp[n-1]) is also stored at total_out when it is not NULL.
+void launch_scan(int* rp, long long n, unsigned long long* tile_state, Counters* ctr, long long* total_out,
+                 cudaStream_t s);
 
 // a2/a4, merge classes (M1 and M2 together): warp tiles of 32 consecutive rows.  `wide` selects the
 // 64-product sort (needed when some merge-class row has more than 32 products).
@@ -39,6 +41,14 @@ void launch_dense_symbolic(const DevCsr& A, const DevCsr& B, const int* list, in
                            int* counts, Counters* ctr, cudaStream_t s);
 void launch_dense_numeric(const DevCsr& A, const DevCsr& B, const int* list, int count, void* slabs, int nslabs,
                           const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s);
+
+// Backward: transpose of A's structure (workspace of transpose_bytes(A.cols, A.nnz)), dA, dB.
+size_t transpose_bytes(int nrows_t, long long nnz);
+void launch_transpose(const DevCsr& A, void* ws, Counters* ctr, cudaStream_t s);
+void launch_grad_a(const DevCsr& A, const DevCsr& B, const int* C_rp, const int* C_col, const double* W, double* dA,
+                   Counters* ctr, cudaStream_t s);
+void launch_grad_b(const DevCsr& A, const DevCsr& B, const void* tws, const int* C_rp, const int* C_col,
+                   const double* W, double* dB, Counters* ctr, cudaStream_t s);
 
 int num_sms();
 

@@ -141,7 +141,8 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS)
-k_scan(int* __restrict__ rp, long long n, unsigned long long* __restrict__ ts, Counters* __restrict__ ctr) {
+k_scan(int* __restrict__ rp, long long n, unsigned long long* __restrict__ ts, Counters* __restrict__ ctr,
+       long long* __restrict__ total_out) {
   __shared__ int s_tile;
   __shared__ long long s_warp[SCAN_THREADS / 32];
   __shared__ long long s_prefix;
@@ -211,15 +212,16 @@ k_scan(int* __restrict__ rp, long long n, unsigned long long* __restrict__ ts, C
       const long long e = off + v[i];
       if (e > INT_MAX) ovf = true;
       rp[idx] = (int)e;
-      if (idx == n - 1) ctr->nnzC = e;
+      if (idx == n - 1 && total_out) *total_out = e;
     }
   }
   if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&ctr->status, ST_OVERFLOW);
 }
 
-void launch_scan(int* rp, long long n, unsigned long long* tile_state, Counters* ctr, cudaStream_t s) {
+void launch_scan(int* rp, long long n, unsigned long long* tile_state, Counters* ctr, long long* total_out,
+                 cudaStream_t s) {
   const long long tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-  k_scan<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(rp, n, tile_state, ctr);
+  k_scan<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(rp, n, tile_state, ctr, total_out);
 }
 
 }  // namespace spg
