@@ -47,6 +47,7 @@ def parse_args():
     ap.add_argument("--workload", default="plain", choices=["plain", "medium"],
                     help="plain: the benchmark workload; medium: Laplacian 1024^2 + random 500K x 8 "
                          "(inputs above L2, a few hundred MB; for profiler captures)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward measurements")
     ap.add_argument("--verbose", action="store_true")
     return ap.parse_args()
 
@@ -339,6 +340,11 @@ def run_ours(args, rank, world, local_rank):
         cpu = {"value": rate, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                "sample": f"first 1/16 of the rows of A in each product, full B ({dt:.1f} s, {F} products)"}
 
+    extras = {}
+    if not args.no_extras and args.workload == "plain":
+        extras["batched"] = run_batched(args, dev, binding, torch)
+        extras["backward"] = run_backward(args, dev, binding, torch)
+
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -350,7 +356,8 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk.summary(), "detail": detail,
             "three_call": {"ms_per_step": ms_3call, "value": world * flop_step / (ms_3call * 1e-3) / 1e9,
                            "path": "plan / symbolic / numeric"},
-            "path": "plan (binning, F read back) + single-pass compute (nnz(C) read back)"}
+            "path": "plan (binning, F read back) + single-pass compute (nnz(C) read back)",
+            **extras}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -407,6 +414,106 @@ def run_e2e(args, prods, dev, stream, binding, torch, world):
     F_total = sum(p["info"]["products"] for p in prods)
     return {"value": world * 2 * F_total / dt / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": steps}
+
+
+def run_batched(args, dev, binding, torch):
+    """512 independent products (half Laplacian^2, half random*random, N log-uniform 256..65536):
+    one graph-replayed batch against the per-matrix loop, default and autotuned row classes."""
+    from paper_1303_1651_gb300 import batched, tune
+    probs = synth.batch_problems(count=512, seed=synth.SEED_BATCH)
+    A, B, lay = batched.concat(probs)
+    dA, dB = binding.DeviceCSR.from_host(A, dev), binding.DeviceCSR.from_host(B, dev)
+    F = None
+    out = {"problems": len(probs), "rows": A.rows, "nnz_A": A.nnz, "nnz_B": B.nnz}
+    steps = max(3, args.steps)
+
+    def time_batch(opt):
+        bp = batched.BatchedProduct(dA, dB, opt)
+        for _ in range(3):
+            bp.run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            bp.run()
+        e1.record()
+        torch.cuda.synchronize()
+        bp.check()
+        f = bp.info["products"]
+        ms = e0.elapsed_time(e1) / steps
+        bp.close()
+        return f, ms
+
+    F, ms = time_batch(None)
+    out["F"] = F
+    out["batched_ms"] = ms
+    out["batched_gflops"] = 2 * F / (ms * 1e-3) / 1e9
+    tuned = tune.tune(dA, dB, cache_path=None)
+    topt = binding.options(**tuned["options"]) if tuned["options"] else None
+    _, tms = time_batch(topt)
+    out["tuned_options"] = tuned["options"]
+    out["tuned_batched_ms"] = tms
+    out["tuned_batched_gflops"] = 2 * F / (tms * 1e-3) / 1e9
+    devp = [(binding.DeviceCSR.from_host(Ap, dev), binding.DeviceCSR.from_host(Bp, dev)) if Bp is not Ap
+            else (lambda d: (d, d))(binding.DeviceCSR.from_host(Ap, dev)) for Ap, Bp in probs]
+    pm = batched.PerMatrix(devp, topt)
+    pm.run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = max(2, min(steps, 5))
+    for _ in range(reps):
+        pm.run()
+    torch.cuda.synchronize()
+    pms = (time.perf_counter() - t0) / reps * 1e3
+    out["per_matrix_ms"] = pms
+    out["per_matrix_gflops"] = 2 * pm.F / (pms * 1e-3) / 1e9
+    out["speedup_batched_vs_per_matrix"] = pms / min(ms, tms)
+    return out
+
+
+def run_backward(args, dev, binding, torch):
+    """C = A*B with A random 262144 x 262144 (16 per row), B the 512 x 512 grid Laplacian;
+    loss = sum(W * C), W ~ N(0, 1) on C's structure: forward + backward (dA and dB)."""
+    A = synth.random_k(262144, 16, synth.SEED_A)
+    B = synth.laplacian5(512)
+    dA, dB = binding.DeviceCSR.from_host(A, dev), binding.DeviceCSR.from_host(B, dev)
+    ws = torch.empty(binding.spgemm_workspace_size(dA, dB), dtype=torch.uint8, device=dev)
+    tws = torch.empty(binding.spgemm_backward_workspace_size(dA, dB), dtype=torch.uint8, device=dev)
+    plan = binding.spgemm_plan(dA, dB, ws)
+    try:
+        F = binding.spgemm_plan_info(plan)["products"]
+        C_rp = torch.empty(A.rows + 1, dtype=torch.int32, device=dev)
+        C_col = torch.empty(F, dtype=torch.int32, device=dev)
+        C_val = torch.empty(F, dtype=torch.float64, device=dev)
+        nnz = binding.spgemm_compute(plan, dA.val, dB.val, C_rp, C_col, C_val)
+        gen = torch.Generator(device=dev).manual_seed(synth.SEED_W)
+        W = torch.randn(nnz, dtype=torch.float64, device=dev, generator=gen)
+        gA = torch.empty(A.nnz, dtype=torch.float64, device=dev)
+        gB = torch.empty(B.nnz, dtype=torch.float64, device=dev)
+        steps = max(3, args.steps)
+        for _ in range(2):
+            binding.spgemm_backward(plan, dA.val, dB.val, W, gA, gB, tws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            binding.spgemm_backward(plan, dA.val, dB.val, W, gA, gB, tws)
+        e1.record()
+        torch.cuda.synchronize()
+        binding.spgemm_status(plan)
+        bms = e0.elapsed_time(e1) / steps
+        # forward (plan + compute, host syncs included)
+        f0 = time.perf_counter()
+        for _ in range(steps):
+            p2 = binding.spgemm_plan(dA, dB, ws)
+            binding.spgemm_compute(p2, dA.val, dB.val, C_rp, C_col, C_val)
+            binding.spgemm_free(p2)
+        fms = (time.perf_counter() - f0) / steps * 1e3
+    finally:
+        binding.spgemm_free(plan)
+    return {"F": F, "nnz_c": nnz, "backward_ms": bms, "backward_gflops": 4 * F / (bms * 1e-3) / 1e9,
+            "forward_ms": fms, "forward_gflops": 2 * F / (fms * 1e-3) / 1e9,
+            "flops_note": "backward does F multiply-adds for dA and F for dB: 4F flops"}
 
 
 def main():
