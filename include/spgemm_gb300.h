@@ -90,7 +90,8 @@ typedef struct {
   int32_t merge_max_k;    /* rows with k_r <= this (max 8) may use the merge classes (default 8) */
   int32_t m1_max_u;       /* class M1 (thread-per-row sort of <= 32 products): u_r <= this (max 32, default 32) */
   int32_t m2_max_u;       /* class M2 (thread-per-row sort of <= 64 products): u_r <= this (max 64, default 64) */
-  int32_t warp_max_u;     /* warp-per-row hash class W: u_r <= this (max 512, default 512) */
+  int32_t warp_max_u;     /* warp-per-row class W (bit vector over the row's column range, or a
+                             hash table): u_r <= this (max 1024, default 1024) */
   int32_t block_max_u;    /* block-per-row hash class B: u_r <= this (max 4096, default 4096);
                              longer rows use a dense accumulator in global memory (class G) */
   int32_t dense_slabs;    /* CTAs (each owning one dense accumulator of B.cols doubles) for class G

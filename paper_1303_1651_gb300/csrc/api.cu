@@ -34,12 +34,12 @@ Layout layout(int m, int ncols, int nslabs) {
 }
 
 Limits limits_from(const spgemm_options_t* o) {
-  Limits l{8, 32, 64, 512, 4096};
+  Limits l{8, 32, 64, 1024, 4096};
   if (o) {
     if (o->merge_max_k > 0) l.merge_k = std::min(o->merge_max_k, 8);
     if (o->m1_max_u > 0) l.m1_u = std::min(o->m1_max_u, 32);
     if (o->m2_max_u > 0) l.m2_u = std::min(o->m2_max_u, 64);
-    if (o->warp_max_u > 0) l.warp_u = std::min(o->warp_max_u, 512);
+    if (o->warp_max_u > 0) l.warp_u = std::min(o->warp_max_u, 1024);
     if (o->block_max_u > 0) l.block_u = std::min(o->block_max_u, 4096);
     if (o->m1_max_u < 0) l.m1_u = -1;     // negative: class disabled (testing hook)
     if (o->m2_max_u < 0) l.m2_u = -1;

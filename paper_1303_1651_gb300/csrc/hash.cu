@@ -62,7 +62,7 @@ struct HashSmem {
   // numeric: vals[T] + cvals[T/2] (doubles), keys[T] + ckeys[T/2] (ints), counter
   static constexpr size_t num_per_group = 8 * T + 8 * (T / 2) + 4 * T + 4 * (T / 2) + 16;
   static constexpr size_t sym_bytes = GPB * sym_per_group + 4 * 32;
-  static constexpr size_t num_bytes = GPB * num_per_group + 4 * 32;
+  static constexpr size_t num_bytes = GPB * num_per_group + 4 * 32 + 16;
 };
 
 template <int GROUP, int LOG2T, int GPB>
@@ -76,10 +76,17 @@ k_hash_sym(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
   int* keys = reinterpret_cast<int*>(smem + g * L::sym_per_group);
   int* s_red = reinterpret_cast<int*>(smem + GPB * L::sym_per_group);
   for (int idx = blockIdx.x * GPB + g; idx < count; idx += gridDim.x * GPB) {
-    for (int i = gt; i < T; i += GROUP) keys[i] = KEY_NONE;
-    group_sync<GROUP>();
     const int r = list[idx];
     const int a0 = A.rp[r], a1 = A.rp[r + 1];
+    // table of pow2 >= 2u slots (at most T)
+    int uu = 0;
+    for (int p = a0 + gt; p < a1; p += GROUP) { const int j = __ldg(A.col + p); uu += __ldg(B.rp + j + 1) - __ldg(B.rp + j); }
+    const int u = group_sum<GROUP>(uu, s_red);
+    unsigned lg = 6;
+    while ((1 << lg) < 2 * u && (1 << lg) < T) ++lg;
+    const int TR = 1 << lg;
+    for (int i = gt; i < TR; i += GROUP) keys[i] = KEY_NONE;
+    group_sync<GROUP>();
     int cnt = 0;
     bool full = false;
     for (int p = a0; p < a1; ++p) {
@@ -87,7 +94,7 @@ k_hash_sym(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
       const int bs = __ldg(B.rp + j), be = __ldg(B.rp + j + 1);
       for (int q = bs + gt; q < be; q += GROUP) {
         bool fresh;
-        const int slot = hash_insert(keys, __ldg(B.col + q), LOG2T, &fresh);
+        const int slot = hash_insert(keys, __ldg(B.col + q), lg, &fresh);
         if (slot < 0) full = true;
         cnt += fresh;
       }
@@ -113,12 +120,19 @@ k_hash_num(DevCsr A, DevCsr B, const int* __restrict__ list, int count, const in
   int* keys = reinterpret_cast<int*>(cvals + T / 2);
   int* ckeys = keys + T;
   int* s_n = ckeys + T / 2;
+  int* s_red = reinterpret_cast<int*>(smem + GPB * L::num_per_group);
   for (int idx = blockIdx.x * GPB + g; idx < count; idx += gridDim.x * GPB) {
-    for (int i = gt; i < T; i += GROUP) { keys[i] = KEY_NONE; vals[i] = 0.0; }
-    if (gt == 0) *s_n = 0;
-    group_sync<GROUP>();
     const int r = list[idx];
     const int a0 = A.rp[r], a1 = A.rp[r + 1];
+    int uu = 0;
+    for (int p = a0 + gt; p < a1; p += GROUP) { const int j = __ldg(A.col + p); uu += __ldg(B.rp + j + 1) - __ldg(B.rp + j); }
+    const int u = group_sum<GROUP>(uu, s_red);
+    unsigned lg = 6;
+    while ((1 << lg) < 2 * u && (1 << lg) < T) ++lg;
+    const int TR = 1 << lg;
+    for (int i = gt; i < TR; i += GROUP) { keys[i] = KEY_NONE; vals[i] = 0.0; }
+    if (gt == 0) *s_n = 0;
+    group_sync<GROUP>();
     bool full = false;
     for (int p = a0; p < a1; ++p) {
       const int j = __ldg(A.col + p);
@@ -126,7 +140,7 @@ k_hash_num(DevCsr A, DevCsr B, const int* __restrict__ list, int count, const in
       const int bs = __ldg(B.rp + j), be = __ldg(B.rp + j + 1);
       for (int q = bs + gt; q < be; q += GROUP) {
         bool fresh;
-        const int slot = hash_insert(keys, __ldg(B.col + q), LOG2T, &fresh);
+        const int slot = hash_insert(keys, __ldg(B.col + q), lg, &fresh);
         if (slot < 0) { full = true; continue; }
         atomicAdd(&vals[slot], __dmul_rn(a, __ldg(B.val + q)));
       }
@@ -134,7 +148,7 @@ k_hash_num(DevCsr A, DevCsr B, const int* __restrict__ list, int count, const in
     if (full) atomicOr(&ctr->status, ST_TABLE_FULL);
     group_sync<GROUP>();
     // compact the touched slots (any order), then sort them by column
-    for (int i = gt; i < T; i += GROUP) {
+    for (int i = gt; i < TR; i += GROUP) {
       const int k = keys[i];
       if (k != KEY_NONE) {
         const int pos = atomicAdd(s_n, 1);
@@ -173,6 +187,327 @@ k_hash_num(DevCsr A, DevCsr B, const int* __restrict__ list, int count, const in
   }
 }
 
+// ---------------------------------------------------------------------------
+// Class W: one warp per row, up to WR_UMAX products.  The row's products are staged in shared
+// memory (a_rj * b_jx computed there, lane-parallel); then, when the row's columns span at most
+// WR_RANGE values, a bit vector over [min, max] orders them -- the "Brute Force"-bool lookup
+// vector of Section IV-B restricted to the MinMax range: per-word prefix popcounts give every
+// column its rank, values are summed at their rank, and the columns come out ascending by
+// scanning the bits.  Wider rows use a hash table sized to the row, compacted in place and sorted
+// by a bitonic network over the distinct columns only.
+// ---------------------------------------------------------------------------
+constexpr int WR_UMAX = 1024;
+constexpr int WR_TMAX = 2048;
+constexpr int WR_RANGE = 65536;
+constexpr int WR_WARPS = 2;
+
+// Bitonic sort of 32*E keys held E per lane: after it, lane l holds sorted positions l*E .. l*E+E-1.
+// Stages with stride < E stay inside a lane (static register indices); wider ones exchange with
+// lane ^ (stride / E) by shuffles.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned (&k)[E]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32 * E; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride >= E) {
+        const int lm = stride / E;
+        const bool lower = (lane & lm) == 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const unsigned other = __shfl_xor_sync(FULL, k[e], lm);
+          const bool up = ((lane * E + e) & size) == 0;
+          k[e] = (up == lower) ? min(k[e], other) : max(k[e], other);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if ((e & stride) == 0) {
+            const int f = e | stride;
+            const bool up = ((lane * E + e) & size) == 0;
+            const unsigned a = k[e], b = k[f];
+            const unsigned lo = min(a, b), hi = max(a, b);
+            k[e] = up ? lo : hi;
+            k[f] = up ? hi : lo;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Register-sort mode of class W: keys (column - mn) << 10 | product index, sorted across the warp;
+// each product's rank among the distinct columns comes from group-start flags; values are added
+// at their rank.  Returns the number of distinct columns; writes the columns (ascending) to outc
+// and their sums to sums (numeric).
+template <int E, bool NUM>
+__device__ __forceinline__ int warp_sort_rank(const int* s_col, const double* s_val, int u, int mn, int* outc,
+                                              double* sums) {
+  const int lane = threadIdx.x & 31;
+  constexpr unsigned PAD = 0xffffffffu;
+  unsigned k[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int g = e * 32 + lane;   // initial placement is free: read lane-contiguous (no bank conflicts)
+    k[e] = g < u ? ((unsigned)(s_col[g] - mn) << 10) | (unsigned)g : PAD;
+  }
+  warp_bitonic<E>(k);
+  // group starts: position p starts a new column if its column differs from position p-1's
+  const unsigned prev_last = __shfl_up_sync(FULL, k[E - 1], 1);
+  int starts = 0;
+  bool st[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const unsigned pk = (e == 0) ? (lane == 0 ? PAD : prev_last) : k[e - 1];
+    st[e] = k[e] != PAD && (lane * E + e == 0 || (k[e] >> 10) != (pk >> 10));
+    starts += st[e];
+  }
+  int total;
+  int rank = warp_excl_scan(starts, &total) - 1;
+  if (NUM) {
+    for (int q = lane; q < total; q += 32) sums[q] = 0.0;
+    __syncwarp();
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (k[e] != PAD) {
+      rank += st[e];
+      if (NUM) {
+        if (st[e]) outc[rank] = mn + (int)(k[e] >> 10);
+        atomicAdd(&sums[rank], s_val[k[e] & 1023u]);
+      }
+    }
+  }
+  __syncwarp();
+  return total;
+}
+
+template <bool NUM>
+struct WarpRowSmem {
+  static constexpr size_t s_val = 0;                                  // double [WR_UMAX] products
+  static constexpr size_t s_col = s_val + (NUM ? 8 * WR_UMAX : 0);    // int    [WR_UMAX] columns
+  static constexpr size_t region = s_col + 4 * WR_UMAX;
+  // bit-vector mode: bits uint[WR_RANGE/32] @0, rank ushort[WR_RANGE/32] @8192, sums double[WR_UMAX] @12288
+  // hash mode:       vals double[WR_TMAX] @0, keys int[WR_TMAX] @16384 (NUM); keys @0 (symbolic)
+  static constexpr size_t region_bytes = NUM ? 24576 : 8192;
+  static constexpr size_t bytes = region + region_bytes;
+};
+
+__device__ __forceinline__ int warp_min_i(int v) { return __reduce_min_sync(FULL, v); }
+__device__ __forceinline__ int warp_max_i(int v) { return __reduce_max_sync(FULL, v); }
+
+template <bool NUM>
+__global__ void __launch_bounds__(WR_WARPS * 32, 1)
+k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __restrict__ rp,
+           int* __restrict__ C_col, double* __restrict__ C_val, Counters* __restrict__ ctr) {
+  using L = WarpRowSmem<NUM>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* wb = smem + (size_t)warp * L::bytes;
+  double* s_val = reinterpret_cast<double*>(wb + L::s_val);
+  int* s_col = reinterpret_cast<int*>(wb + L::s_col);
+  unsigned char* reg = wb + L::region;
+  for (int idx = blockIdx.x * WR_WARPS + warp; idx < count; idx += gridDim.x * WR_WARPS) {
+    const int r = list[idx];
+    const int a0 = __ldg(A.rp + r), a1 = __ldg(A.rp + r + 1);
+    // 1. stage the products, 32 runs (entries of A) at a time
+    int u = 0, mn = INT_MAX, mx = -1;
+    bool over = false;
+    for (int c0 = a0; c0 < a1; c0 += 32) {
+      const int e = c0 + lane;
+      int bs = 0, len = 0;
+      double a = 0.0;
+      if (e < a1) {
+        const int j = __ldg(A.col + e);
+        bs = __ldg(B.rp + j);
+        len = __ldg(B.rp + j + 1) - bs;
+        if (NUM) a = __ldg(A.val + e);
+      }
+      int tot;
+      const int off = warp_excl_scan(len, &tot);
+      if (u + tot > WR_UMAX) { over = true; break; }   // class limits make this unreachable
+      for (int cb = 0; cb < tot; cb += 32) {
+        const int q = cb + lane;
+        int t = 0;   // last run whose offset is <= q (empty runs share the next run's offset)
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int cnd = t + step;
+          if (__shfl_sync(FULL, off, cnd) <= q) t = cnd;
+        }
+        const int sp = __shfl_sync(FULL, bs, t) + (q - __shfl_sync(FULL, off, t));
+        const double at = NUM ? __shfl_sync(FULL, a, t) : 0.0;
+        if (q < tot) {
+          const int x = __ldg(B.col + sp);
+          s_col[u + q] = x;
+          if (NUM) s_val[u + q] = __dmul_rn(at, __ldg(B.val + sp));
+          mn = min(mn, x);
+          mx = max(mx, x);
+        }
+      }
+      u += tot;
+    }
+    if (over) {
+      if (lane == 0) atomicOr(&ctr->status, ST_TABLE_FULL);
+      continue;
+    }
+    mn = warp_min_i(mn);
+    mx = warp_max_i(mx);
+    __syncwarp();
+    int cnt = 0;
+    int g0 = 0, g1 = 0;
+    if (NUM) { g0 = __ldg(rp + r); g1 = __ldg(rp + r + 1); }
+    const long long range = (long long)mx - (long long)mn + 1;
+    // Choice of ordering (the "Combined" idea of Section IV-B): the bit vector when the column
+    // range is small next to the row (at most 4u words), a register sort when the keys fit 32
+    // bits, a hash table otherwise.
+    const bool bitvec = range <= WR_RANGE && (range >> 5) <= 4 * (long long)u;
+    const bool regsort = !bitvec && range < (1 << 22);
+    if (u > 0 && regsort) {
+      int* outc = reinterpret_cast<int*>(reg + 8192);
+      double* sums = reinterpret_cast<double*>(reg + 12288);
+      if (u <= 128) cnt = warp_sort_rank<4, NUM>(s_col, s_val, u, mn, outc, sums);
+      else if (u <= 256) cnt = warp_sort_rank<8, NUM>(s_col, s_val, u, mn, outc, sums);
+      else if (u <= 512) cnt = warp_sort_rank<16, NUM>(s_col, s_val, u, mn, outc, sums);
+      else cnt = warp_sort_rank<32, NUM>(s_col, s_val, u, mn, outc, sums);
+      if (NUM) {
+        if (lane == 0 && g1 - g0 != cnt) atomicOr(&ctr->status, ST_MISMATCH);
+        for (int q = lane; q < cnt && g0 + q < g1; q += 32) {
+          C_col[g0 + q] = outc[q];
+          C_val[g0 + q] = sums[q];
+        }
+      }
+    } else if (u > 0 && bitvec) {
+      // 2a. bit vector over [mn, mx]
+      unsigned* bits = reinterpret_cast<unsigned*>(reg);
+      unsigned short* rank = reinterpret_cast<unsigned short*>(reg + 8192);
+      const int W = (int)((range + 31) >> 5);
+      for (int w = lane; w < W; w += 32) bits[w] = 0u;
+      __syncwarp();
+      for (int q = lane; q < u; q += 32) {
+        const int d = s_col[q] - mn;
+        atomicOr(&bits[d >> 5], 1u << (d & 31));
+      }
+      __syncwarp();
+      int base = 0;
+      for (int w0 = 0; w0 < W; w0 += 32) {
+        const int w = w0 + lane;
+        const unsigned b = w < W ? bits[w] : 0u;
+        int t2;
+        const int ex = warp_excl_scan(__popc(b), &t2);
+        if (NUM && w < W) rank[w] = (unsigned short)(base + ex);
+        base += t2;
+      }
+      cnt = base;
+      if (NUM) {
+        double* sums = reinterpret_cast<double*>(reg + 12288);
+        for (int q = lane; q < cnt; q += 32) sums[q] = 0.0;
+        __syncwarp();
+        for (int q = lane; q < u; q += 32) {
+          const int d = s_col[q] - mn;
+          const int w = d >> 5;
+          const int k = rank[w] + __popc(bits[w] & ((1u << (d & 31)) - 1u));
+          atomicAdd(&sums[k], s_val[q]);
+        }
+        __syncwarp();
+        if (lane == 0 && g1 - g0 != cnt) atomicOr(&ctr->status, ST_MISMATCH);
+        for (int w0 = 0; w0 < W; w0 += 32) {
+          const int w = w0 + lane;
+          unsigned b = w < W ? bits[w] : 0u;
+          int k = w < W ? (int)rank[w] : 0;
+          while (b) {
+            const int bit = __ffs(b) - 1;
+            b &= b - 1;
+            if (k < g1 - g0) {
+              C_col[g0 + k] = mn + (w << 5) + bit;
+              C_val[g0 + k] = sums[k];
+            }
+            ++k;
+          }
+        }
+      }
+    } else if (u > 0) {
+      // 2b. hash table of T = pow2 >= 2u slots
+      int logT = 6;
+      while ((1 << logT) < 2 * u) ++logT;
+      const int T = 1 << logT;
+      int* keys = reinterpret_cast<int*>(reg + (NUM ? 16384 : 0));
+      double* vals = reinterpret_cast<double*>(reg);
+      for (int i = lane; i < T; i += 32) { keys[i] = KEY_NONE; if (NUM) vals[i] = 0.0; }
+      __syncwarp();
+      int mine = 0;
+      bool full = false;
+      for (int q = lane; q < u; q += 32) {
+        bool fresh;
+        const int slot = hash_insert(keys, s_col[q], (unsigned)logT, &fresh);
+        if (slot < 0) { full = true; continue; }
+        mine += fresh;
+        if (NUM) atomicAdd(&vals[slot], s_val[q]);
+      }
+      if (__any_sync(FULL, full) && lane == 0) atomicOr(&ctr->status, ST_TABLE_FULL);
+      cnt = __reduce_add_sync(FULL, mine);
+      __syncwarp();
+      if (NUM) {
+        // compact in slot order (in place: every entry moves down), then sort the distinct columns
+        int wr = 0;
+        for (int i0 = 0; i0 < T; i0 += 32) {
+          const int i = i0 + lane;
+          const int k = keys[i];
+          const double v = vals[i];
+          const bool valid = k != KEY_NONE;
+          const unsigned m = __ballot_sync(FULL, valid);
+          const int pos = wr + __popc(m & lanemask_lt());
+          __syncwarp();
+          if (valid) { keys[pos] = k; vals[pos] = v; }
+          wr += __popc(m);
+          __syncwarp();
+        }
+        int n2 = 1;
+        while (n2 < cnt) n2 <<= 1;
+        for (int i = cnt + lane; i < n2; i += 32) { keys[i] = KEY_NONE; vals[i] = 0.0; }
+        __syncwarp();
+        for (int kk = 2; kk <= n2; kk <<= 1) {
+          for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int i = lane; i < n2; i += 32) {
+              const int ixj = i ^ jj;
+              if (ixj > i) {
+                const int ki = keys[i], kj = keys[ixj];
+                if ((ki > kj) == ((i & kk) == 0)) {
+                  keys[i] = kj; keys[ixj] = ki;
+                  const double t = vals[i]; vals[i] = vals[ixj]; vals[ixj] = t;
+                }
+              }
+            }
+            __syncwarp();
+          }
+        }
+        if (lane == 0 && g1 - g0 != cnt) atomicOr(&ctr->status, ST_MISMATCH);
+        for (int i = lane; i < cnt && g0 + i < g1; i += 32) {
+          C_col[g0 + i] = keys[i];
+          C_val[g0 + i] = vals[i];
+        }
+      }
+    } else if (NUM && lane == 0 && g1 != g0) {
+      atomicOr(&ctr->status, ST_MISMATCH);
+    }
+    if (!NUM && lane == 0) rp[r] = cnt;
+    __syncwarp();
+  }
+}
+
+template <bool NUM>
+static void launch_warp_row(const DevCsr& A, const DevCsr& B, const int* list, int count, int* rp, int* C_col,
+                            double* C_val, Counters* ctr, cudaStream_t s) {
+  if (count <= 0) return;
+  constexpr size_t bytes = (size_t)WR_WARPS * WarpRowSmem<NUM>::bytes;
+  auto kern = k_warp_row<NUM>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WR_WARPS * 32, bytes);
+  const int blocks = std::max(1, std::min((count + WR_WARPS - 1) / WR_WARPS, num_sms() * std::max(per_sm, 1)));
+  kern<<<blocks, WR_WARPS * 32, bytes, s>>>(A, B, list, count, rp, C_col, C_val, ctr);
+}
+
 template <int GROUP, int LOG2T, int GPB, bool NUM>
 static void launch_hash(const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts, const int* rp,
                         int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
@@ -197,13 +532,13 @@ static void launch_hash(const DevCsr& A, const DevCsr& B, const int* list, int c
 
 void launch_hash_symbolic(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts,
                           Counters* ctr, cudaStream_t s) {
-  if (cls == CLS_W) launch_hash<32, 10, 8, false>(A, B, list, count, counts, nullptr, nullptr, nullptr, ctr, s);
+  if (cls == CLS_W) launch_warp_row<false>(A, B, list, count, counts, nullptr, nullptr, ctr, s);
   else launch_hash<512, 13, 1, false>(A, B, list, count, counts, nullptr, nullptr, nullptr, ctr, s);
 }
 
 void launch_hash_numeric(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, const int* rp,
                          int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
-  if (cls == CLS_W) launch_hash<32, 10, 4, true>(A, B, list, count, nullptr, rp, C_col, C_val, ctr, s);
+  if (cls == CLS_W) launch_warp_row<true>(A, B, list, count, const_cast<int*>(rp), C_col, C_val, ctr, s);
   else launch_hash<512, 13, 1, true>(A, B, list, count, nullptr, rp, C_col, C_val, ctr, s);
 }
 

@@ -224,3 +224,16 @@ def test_fused_then_numeric_with_new_values():
         compare(got, oracle.spgemm(A2, B), single=True)
     finally:
         binding.spgemm_free(plan)
+
+
+@PATHS
+@pytest.mark.parametrize("ncols,k", [(2000, 12), (300_000, 12), (300_000, 30), (6_000_000, 10)],
+                         ids=["bitvector", "regsort-128", "regsort-1024", "hash"])
+def test_warp_class_orderings(ncols, k, fused):
+    # rows of k entries of A times rows of k entries of B: u = k^2 products, warp class W;
+    # the column range of B picks the ordering (bit vector / register sort / hash table)
+    A = synth.random_k(700, k, 81, ncols=400)
+    B = synth.random_k(400, k, 82, ncols=ncols)
+    C = gpu_product(A, B, fused=fused)
+    assert C["info"]["rows_per_class"]["W"] == 700
+    compare(C, oracle.spgemm(A, B), single=True)
