@@ -98,7 +98,12 @@ typedef struct {
                              (default 2) */
   int32_t validate;       /* nonzero: also check row_ptr monotonicity and every column index of A and
                              B before planning (one extra pass over both matrices) */
-  int32_t reserved[9];
+  int32_t merge_values;   /* classes M1/M2: 0 automatic (default: values of B read in the reduce for
+                             32-product tiles, staged in shared memory for 64-product tiles), 1 read
+                             from B in the reduce and C written from there (less shared memory, more
+                             warps; best when neighbouring rows of A reach neighbouring rows of B),
+                             2 staged with the columns and C written by a coalesced pass */
+  int32_t reserved[8];
 } spgemm_options_t;
 
 /* Counters of a plan, valid after spgemm_plan (and nnz_c after spgemm_symbolic). */

@@ -41,7 +41,7 @@ class spgemm_csr_t(ctypes.Structure):
 class spgemm_options_t(ctypes.Structure):
     _fields_ = [("merge_max_k", ctypes.c_int32), ("m1_max_u", ctypes.c_int32), ("m2_max_u", ctypes.c_int32),
                 ("warp_max_u", ctypes.c_int32), ("block_max_u", ctypes.c_int32), ("dense_slabs", ctypes.c_int32),
-                ("validate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("validate", ctypes.c_int32), ("merge_values", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
 
 
 class spgemm_info_t(ctypes.Structure):

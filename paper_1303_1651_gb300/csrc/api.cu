@@ -92,6 +92,7 @@ struct spgemm_plan_s {
   DevCsr A{}, B{};
   Limits lim{};
   int nslabs = 0;
+  int values_mode = 0;          // merge classes: 0 automatic, 1 values read from B, 2 staged
   Layout L{};
   unsigned char* ws = nullptr;
   Counters* ctr = nullptr;
@@ -147,6 +148,7 @@ spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spg
   p->B = to_dev(*B);
   p->lim = limits_from(opt);
   p->nslabs = nslabs;
+  p->values_mode = (opt && opt->merge_values >= 0 && opt->merge_values <= 2) ? opt->merge_values : 0;
   p->L = L;
   p->ws = (unsigned char*)workspace;
   p->ctr = (Counters*)(p->ws + L.ctr);
@@ -223,7 +225,8 @@ spgemm_status_t spgemm_numeric(spgemm_plan_t p, const double* A_val, const doubl
   uint8_t* cls = p->ws + L.cls;
   const int wide = p->h.max_u_merge > 32;
   if (p->ev_start) cudaEventRecord(p->ev_start, s);
-  if (cnt[CLS_M1] + cnt[CLS_M2] > 0) launch_merge_numeric(wide, A, B, cls, p->C_rp, C_col, C_val, p->ctr, s);
+  if (cnt[CLS_M1] + cnt[CLS_M2] > 0)
+    launch_merge_numeric(wide, p->values_mode, A, B, cls, p->C_rp, C_col, C_val, p->ctr, s);
   if (cnt[CLS_W] > 0)
     launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s);
   if (cnt[CLS_B] > 0)
@@ -270,7 +273,7 @@ static spgemm_status_t compute_enqueue(spgemm_plan_t p, const double* A_val, con
       launch_dense_symbolic(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs,
                             C_row_ptr, p->ctr, s);
     const int wide = p->h.max_u_merge > 32;
-    launch_merge_fused(wide, A, B, cls, C_row_ptr, C_col, C_val, capacity,
+    launch_merge_fused(wide, p->values_mode, A, B, cls, C_row_ptr, C_col, C_val, capacity,
                        (unsigned long long*)(p->ws + L.fused), p->ctr, s);
     if (cnt[CLS_W] > 0)
       launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, C_col, C_val, p->ctr, s);

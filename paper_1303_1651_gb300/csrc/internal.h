@@ -17,15 +17,17 @@ void launch_scan(int* rp, long long n, unsigned long long* tile_state, Counters*
                  cudaStream_t s);
 
 // a2/a4, merge classes (M1 and M2 together): warp tiles of 32 consecutive rows.  `wide` selects the
-// 64-product sort (needed when some merge-class row has more than 32 products).
+// 64-product sort (needed when some merge-class row has more than 32 products).  values_mode:
+// 0 = automatic (values read from B in the reduce for 32-product tiles, staged for 64), 1 = read
+// from B (C written from the reduce), 2 = staged in shared memory (C written by a coalesced pass).
 void launch_merge_symbolic(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* counts,
                            Counters* ctr, cudaStream_t s);
-void launch_merge_numeric(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, const int* rp,
-                          int* C_col, double* C_val, Counters* ctr, cudaStream_t s);
+void launch_merge_numeric(int wide, int values_mode, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls,
+                          const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s);
 // Fused single pass: numeric for merge-class rows, C's row pointer for every row (rows of other classes
 // bring their counts in rp), entries written into C_col/C_val of `capacity` entries.  Uses ctr->ticket.
-void launch_merge_fused(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* rp, int* C_col,
-                        double* C_val, long long capacity, unsigned long long* tile_state, Counters* ctr,
+void launch_merge_fused(int wide, int values_mode, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* rp,
+                        int* C_col, double* C_val, long long capacity, unsigned long long* tile_state, Counters* ctr,
                         cudaStream_t s);
 size_t fused_tile_state_bytes(int rows);
 

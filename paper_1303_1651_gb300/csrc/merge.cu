@@ -46,17 +46,20 @@ constexpr long long FUSED_SPIN_LIMIT = 1LL << 24;
 
 enum MergeMode { MODE_SYM = 0, MODE_NUM = 1, MODE_FUSED = 2 };
 
-template <int MODE, int N>
+template <int MODE, int N, bool DIRECT = false>
 struct SortSmem {
   // Staging: row t's products are contiguous, at pofs_t + t (one slot of skew per row keeps
-  // lanes that read the same position of their rows on different banks).
+  // lanes that read the same position of their rows on different banks).  DIRECT kernels stage
+  // only the columns: values are read from B in the reduce and C is written from there.
   static constexpr int SLOTS = 32 * N + 32;
   static constexpr bool V = MODE != MODE_SYM;
+  static constexpr bool SV = V && !DIRECT;                          // values staged
   static constexpr size_t s_val = 0;                               // double [SLOTS]  b_jx, later group sums
-  static constexpr size_t s_col = s_val + (V ? 8 * SLOTS : 0);     // uint   [SLOTS]  columns, later output keys
+  static constexpr size_t s_col = s_val + (SV ? 8 * SLOTS : 0);    // uint   [SLOTS]  columns, later output keys
   static constexpr size_t r_run = s_col + 4 * SLOTS;               // int2   [MAXR]   (first B entry, start << 8 | lane)
-  static constexpr size_t bytes = r_run + 8 * MAXR;                // s_a (double [8][32], a_rj by run rank and
-                                                                   // lane) reuses r_run after the expand
+  static constexpr size_t s_bofs = r_run + 8 * MAXR;               // int    [8][32]  (DIRECT) B offset of a run rank
+  static constexpr size_t bytes = s_bofs + (DIRECT ? 4 * 8 * 32 : 0);  // s_a (double [8][32], a_rj by run rank
+                                                                   // and lane) reuses r_run after the expand
   static_assert(8 * 8 * 32 <= 8 * MAXR, "a table must fit in the run table");
 };
 
@@ -136,9 +139,9 @@ struct MergeArgs {
   Counters* ctr;
 };
 
-template <int MODE, int N, int WARPS>
+template <int MODE, int N, int WARPS, bool DIRECT>
 __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigned char* wb) {
-  using L = SortSmem<MODE, N>;
+  using L = SortSmem<MODE, N, DIRECT>;
   constexpr bool V = L::V;
   constexpr int IB = (N == 32) ? 5 : 6;     // product-index bits of a key
   constexpr int KB = IB + 3;                // + run-index bits: key = col << KB | run << IB | index
@@ -148,6 +151,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
   unsigned* s_col = reinterpret_cast<unsigned*>(wb + L::s_col);
   int2* r_run = reinterpret_cast<int2*>(wb + L::r_run);
   double* s_a = reinterpret_cast<double*>(wb + L::r_run);
+  int* s_bofs = reinterpret_cast<int*>(wb + L::s_bofs);
   const DevCsr& A = g.A;
   const DevCsr& B = g.B;
 
@@ -219,7 +223,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
       const int sp = rr.x + (p - (rr.y >> 8));
       const int d = p + (rr.y & 31);      // product p of row t lives at slot p + t
       cp_async4(s_col + d, B.col + sp);
-      if (V) cp_async8(s_val + d, B.val + sp);
+      if (L::SV) cp_async8(s_val + d, B.val + sp);
     }
     e_cur = __shfl_sync(FULL, e, 31);
   }
@@ -237,6 +241,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
       if (len[i] > 0) {
         if (d > 0) starts |= 1ull << d;
         if (V) s_a[q * 32 + lane] = av[i];
+        if (DIRECT) s_bofs[q * 32 + lane] = src[i] - d;   // b of product index x of this run: B.val[bofs + x]
         ++q;
       }
       d += len[i];
@@ -268,6 +273,65 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
   int TA = 0;
   const int oa = (MODE == MODE_FUSED) ? warp_excl_scan(mycount, &TA) : 0;
   if (MODE == MODE_FUSED) tile_publish(g.tile_state, tile, TA);
+
+  if constexpr (DIRECT) {
+    // 5'. place first (the offset in C is needed to store from the reduce), then reduce: values
+    //     straight from B, each finished entry straight to C.
+    long long gstart = 0;
+    int lim = INT_MAX;
+    if (MODE == MODE_NUM) {
+      gstart = gbeg;
+      lim = gend - gbeg;
+      if (mine && lim != cnt) atomicOr(&g.ctr->status, ST_MISMATCH);
+    } else {
+      const int mycount = mine ? cnt : other;
+      int TA;
+      const int oa = warp_excl_scan(mycount, &TA);
+      const long long off = tile_lookback(g.tile_state, tile, TA, g.ctr);
+      gstart = off + oa;
+      if (inrange) {
+        if (gstart + mycount > INT_MAX) atomicOr(&g.ctr->status, ST_OVERFLOW);
+        g.rp[r] = (int)gstart;
+        if (r == A.rows - 1) {
+          g.rp[r + 1] = (int)(gstart + mycount);
+          g.ctr->nnzC = gstart + mycount;
+        }
+      }
+      if (off + TA > g.capacity) {
+        if (lane == 0) atomicOr(&g.ctr->status, ST_OVERFLOW);
+        return;
+      }
+    }
+    const int umax = __reduce_max_sync(FULL, u);
+    int o = 0;
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      if (j < umax) {
+        const unsigned kj = key[j];
+        const bool valid = kj != PAD;
+        const int idx = (int)(kj & (unsigned)(N - 1));
+        const int run = (int)((kj >> IB) & 7u);
+        double a = 0.0, b = 0.0;
+        if (valid) {
+          b = __ldg(B.val + s_bofs[run * 32 + lane] + idx);
+          a = s_a[run * 32 + lane];
+        }
+        const bool same = (j < 32) ? ((samemask_lo >> j) & 1u) : ((samemask_hi >> (j - 32)) & 1u);
+        acc = __fma_rn(a, b, same ? acc : 0.0);
+        bool next_same = false;
+        if (j + 1 < N) next_same = ((j + 1) < 32) ? ((samemask_lo >> (j + 1)) & 1u) : ((samemask_hi >> (j + 1 - 32)) & 1u);
+        if (valid && !next_same) {
+          if (o < lim) {
+            g.C_col[gstart + o] = (int)(kj >> KB);
+            g.C_val[gstart + o] = acc;
+          }
+          ++o;
+        }
+      }
+    }
+    return;
+  }
 
   // 5. reduce: acc = fma(a_rj, b_jx, acc) along each group in product order, the first product
   //    added to +0.0 (the dense accumulator's start).  One FP64 instruction per sorted position,
@@ -370,16 +434,16 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
   }
 }
 
-template <int MODE, int N, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
+template <int MODE, int N, int WARPS, bool DIRECT>
+__global__ void __launch_bounds__(WARPS * 32, 1)
 k_merge(MergeArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* wb = smem + (size_t)warp * SortSmem<MODE, N>::bytes;
+  unsigned char* wb = smem + (size_t)warp * SortSmem<MODE, N, DIRECT>::bytes;
   const int ntiles = (g.A.rows + 31) >> 5;
   if (MODE != MODE_FUSED) {
     for (int tile = blockIdx.x * WARPS + warp; tile < ntiles; tile += gridDim.x * WARPS) {
-      merge_tile<MODE, N, WARPS>(g, tile, wb);
+      merge_tile<MODE, N, WARPS, DIRECT>(g, tile, wb);
       __syncwarp();
     }
   } else {
@@ -390,16 +454,16 @@ k_merge(MergeArgs g) {
       if (lane == 0) tile = (int)atomicAdd(&g.ctr->ticket, 1u);
       tile = __shfl_sync(FULL, tile, 0);
       if (tile >= ntiles) break;
-      merge_tile<MODE, N, WARPS>(g, tile, wb);
+      merge_tile<MODE, N, WARPS, DIRECT>(g, tile, wb);
       __syncwarp();
     }
   }
 }
 
-template <int MODE, int N, int WARPS>
+template <int MODE, int N, int WARPS, bool DIRECT = false>
 static void launch_merge(const MergeArgs& g, cudaStream_t s) {
-  constexpr size_t bytes = (size_t)WARPS * SortSmem<MODE, N>::bytes;
-  auto kern = k_merge<MODE, N, WARPS>;
+  constexpr size_t bytes = (size_t)WARPS * SortSmem<MODE, N, DIRECT>::bytes;
+  auto kern = k_merge<MODE, N, WARPS, DIRECT>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   const int ntiles = (g.A.rows + 31) / 32;
   int per_sm = 0;
@@ -425,19 +489,31 @@ void launch_merge_symbolic(int wide, const DevCsr& A, const DevCsr& B, const uin
   else launch_merge<MODE_SYM, 64, 4>(g, s);
 }
 
-void launch_merge_numeric(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, const int* rp,
-                          int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
+void launch_merge_numeric(int wide, int values_mode, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls,
+                          const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
   MergeArgs g{A, B, rowcls, const_cast<int*>(rp), C_col, C_val, 0, nullptr, ctr};
-  if (!wide) launch_merge<MODE_NUM, 32, 1>(g, s);
-  else launch_merge<MODE_NUM, 64, 1>(g, s);
+  const bool direct = values_mode == 1 || (values_mode == 0 && !wide);
+  if (direct) {
+    if (!wide) launch_merge<MODE_NUM, 32, 1, true>(g, s);
+    else launch_merge<MODE_NUM, 64, 1, true>(g, s);
+  } else {
+    if (!wide) launch_merge<MODE_NUM, 32, 1>(g, s);
+    else launch_merge<MODE_NUM, 64, 1>(g, s);
+  }
 }
 
-void launch_merge_fused(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* rp, int* C_col,
-                        double* C_val, long long capacity, unsigned long long* tile_state, Counters* ctr,
+void launch_merge_fused(int wide, int values_mode, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* rp,
+                        int* C_col, double* C_val, long long capacity, unsigned long long* tile_state, Counters* ctr,
                         cudaStream_t s) {
   MergeArgs g{A, B, rowcls, rp, C_col, C_val, capacity, tile_state, ctr};
-  if (!wide) launch_merge<MODE_FUSED, 32, 1>(g, s);
-  else launch_merge<MODE_FUSED, 64, 1>(g, s);
+  const bool direct = values_mode == 1 || (values_mode == 0 && !wide);
+  if (direct) {
+    if (!wide) launch_merge<MODE_FUSED, 32, 1, true>(g, s);
+    else launch_merge<MODE_FUSED, 64, 1, true>(g, s);
+  } else {
+    if (!wide) launch_merge<MODE_FUSED, 32, 1>(g, s);
+    else launch_merge<MODE_FUSED, 64, 1>(g, s);
+  }
 }
 
 }  // namespace spg

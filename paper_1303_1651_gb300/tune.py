@@ -21,7 +21,10 @@ import torch
 from . import binding
 
 CANDIDATES = [
-    {},                                           # defaults: M1 <= 32, M2 <= 64, W <= 512, B <= 4096
+    {},                                           # defaults: M1 <= 32, M2 <= 64, W <= 1024, B <= 4096
+    {"merge_values": 1},                          # merge classes read B's values in the reduce
+    {"merge_values": 2},                          # merge classes stage B's values
+    {"m2_max_u": 32, "merge_values": 1},
     {"m2_max_u": 32},                             # 33..64-product rows to the warp hash (32-product tiles)
     {"m1_max_u": 16, "m2_max_u": 32},
     {"merge_max_k": 4},

@@ -237,3 +237,17 @@ def test_warp_class_orderings(ncols, k, fused):
     C = gpu_product(A, B, fused=fused)
     assert C["info"]["rows_per_class"]["W"] == 700
     compare(C, oracle.spgemm(A, B), single=True)
+
+
+@PATHS
+@pytest.mark.parametrize("mode", [1, 2], ids=["values-from-B", "values-staged"])
+def test_merge_value_modes(mode, fused):
+    # both ways of reading B's values in the sort classes, on short (32) and long (64) tiles
+    L = synth.laplacian5(50)
+    compare(gpu_product(L, L, opts(merge_values=mode), fused=fused), oracle.spgemm(L, L), exact=True)
+    for k in (3, 8):
+        A, B = synth.random_k(3000, k, 90 + k, ncols=2500), synth.random_k(2500, k, 91 + k)
+        compare(gpu_product(A, B, opts(merge_values=mode), fused=fused), oracle.spgemm(A, B), single=True)
+    A = synth.duplicate_entries(synth.random_k(900, 5, 95), 96)
+    Bs = synth.shuffle_rows(synth.random_k(900, 6, 97), 98)
+    compare(gpu_product(A, Bs, opts(merge_values=mode), fused=fused), oracle.spgemm(A, Bs))
