@@ -67,7 +67,8 @@ typedef enum {
   SPGEMM_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
   SPGEMM_ERR_STATE = 7,       /* calls made out of order (numeric before symbolic, ...) */
   SPGEMM_ERR_UNSORTED = 8,    /* reserved (inputs need not be sorted; not returned by this version) */
-  SPGEMM_ERR_MISMATCH = 9     /* numeric found a different structure than symbolic (inputs changed) */
+  SPGEMM_ERR_MISMATCH = 9,    /* numeric found a different structure than symbolic (inputs changed) */
+  SPGEMM_ERR_SCRATCH_LIMIT = 10 /* a size exceeds the fixed scratch of spgemm_scan_counts_noalloc */
 } spgemm_status_t;
 
 /* A CSR matrix in device memory.  row_ptr has rows+1 entries with row_ptr[0] = 0 and
@@ -212,6 +213,44 @@ spgemm_status_t spgemm_plan_set_events(spgemm_plan_t plan, void* start_event, vo
 
 /* Release the plan object.  The workspace stays the caller's.  NULL is accepted. */
 spgemm_status_t spgemm_free(spgemm_plan_t plan);
+
+/* Row pointers from per-row counts, without a workspace and without allocating.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers that can neither
+ * allocate device memory nor lend a workspace when they call, for instance code running where
+ * another framework's pooling allocator has reserved the device memory, or a service that keeps
+ * a fixed memory footprint after start-up.  For them an allocation at call time could fail, or
+ * would change a footprint they must hold constant.
+ *
+ * It performs the step that spgemm_symbolic uses to turn the per-row entry counts of C into C's
+ * row pointers: an exclusive prefix sum over rows (the contiguous row-by-row storage of C,
+ * Section IV-B), by the same single-pass scan kernel.  Instead of a workspace, the scan's scratch
+ * (one state word per 2048 rows plus a 256-byte header) lives in a fixed device array of
+ * SPGEMM_NOALLOC_SCRATCH_BYTES bytes, which every device that runs this call keeps until the
+ * process exits.  That array bounds the size: at most SPGEMM_NOALLOC_MAX_ROWS rows.
+ *
+ *   row_ptr  DEVICE, rows + 1 int32, caller-owned, updated in place.  On entry row_ptr[r] is the
+ *            count of row r (>= 0) for r < rows; row_ptr[rows] is ignored.  On return row_ptr[r]
+ *            is the sum of the counts of rows 0 .. r-1, so row_ptr[0] = 0 and row_ptr[rows] is
+ *            the total.
+ *   rows     number of rows, 0 <= rows <= SPGEMM_NOALLOC_MAX_ROWS.
+ *   total    HOST, may be NULL: receives the total as a 64-bit count (also on OVERFLOW).
+ *   stream   cudaStream_t of the current device.  The call synchronises it before it returns.
+ *
+ * Errors: INVALID (row_ptr NULL, rows < 0); SCRATCH_LIMIT (rows > SPGEMM_NOALLOC_MAX_ROWS:
+ * rejected before any CUDA call, row_ptr untouched); OVERFLOW (a prefix sum exceeds INT32_MAX,
+ * row_ptr then holds truncated values); TIMEOUT; CUDA.
+ *
+ * Set-up: the first call on a device looks up the device address of the scratch array with that
+ * device current, and later calls on the device reuse it.  Make that first call before any
+ * stream capture begins.
+ *
+ * Concurrency: all calls on one device share the one scratch array.  Calls that overlap in time,
+ * from several host threads or on several streams, race on it and give wrong results: serialise
+ * them. */
+#define SPGEMM_NOALLOC_MAX_ROWS 67108863          /* 2^26 - 1 */
+#define SPGEMM_NOALLOC_SCRATCH_BYTES 262400       /* 256 + 8 * 2^26 / 2048 */
+spgemm_status_t spgemm_scan_counts_noalloc(int32_t* row_ptr, int64_t rows, int64_t* total, void* stream);
 
 /* Static string naming a status code. */
 const char* spgemm_error_string(int code);

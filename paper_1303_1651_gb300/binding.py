@@ -21,7 +21,7 @@ _lib = None
 SPGEMM_STATUS = {
     0: "SPGEMM_OK", 1: "SPGEMM_ERR_INVALID", 2: "SPGEMM_ERR_ALLOC", 3: "SPGEMM_ERR_OVERFLOW",
     4: "SPGEMM_ERR_TABLE_FULL", 5: "SPGEMM_ERR_CUDA", 6: "SPGEMM_ERR_TIMEOUT", 7: "SPGEMM_ERR_STATE",
-    8: "SPGEMM_ERR_UNSORTED", 9: "SPGEMM_ERR_MISMATCH",
+    8: "SPGEMM_ERR_UNSORTED", 9: "SPGEMM_ERR_MISMATCH", 10: "SPGEMM_ERR_SCRATCH_LIMIT",
 }
 CLASS_NAMES = ("M1", "M2", "W", "B", "G")
 
@@ -77,13 +77,14 @@ def load():
         lib.spgemm_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         lib.spgemm_plan_info.argtypes = [vp, P(spgemm_info_t)]
         lib.spgemm_free.argtypes = [vp]
+        lib.spgemm_scan_counts_noalloc.argtypes = [vp, ctypes.c_int64, P(ctypes.c_int64), vp]
         lib.spgemm_error_string.argtypes = [ctypes.c_int]
         lib.spgemm_error_string.restype = ctypes.c_char_p
         lib.spgemm_version.restype = ctypes.c_int32
         for name in ("spgemm_workspace_size", "spgemm_plan", "spgemm_symbolic", "spgemm_numeric",
                      "spgemm_compute", "spgemm_status", "spgemm_plan_info", "spgemm_free",
                      "spgemm_plan_set_events", "spgemm_compute_async", "spgemm_backward_workspace_size",
-                     "spgemm_backward"):
+                     "spgemm_backward", "spgemm_scan_counts_noalloc"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -237,6 +238,21 @@ def spgemm_plan_set_events(plan: int, start=None, stop=None):
 def spgemm_free(plan: int):
     if plan:
         load().spgemm_free(plan)
+
+
+def spgemm_scan_counts_noalloc(row_ptr: torch.Tensor, rows: int | None = None, stream=None) -> int:
+    """In place: per-row counts in row_ptr[:rows] -> row pointers in row_ptr[:rows + 1]; returns the
+    total.  Uses the library's fixed scratch array, so nothing is allocated; calls must not overlap."""
+    if rows is None:
+        rows = row_ptr.numel() - 1
+    if row_ptr.dtype != torch.int32 or not row_ptr.is_cuda or not row_ptr.is_contiguous():
+        raise ValueError("row_ptr must be a contiguous int32 CUDA tensor")
+    if rows + 1 > row_ptr.numel():
+        raise ValueError(f"row_ptr holds {row_ptr.numel()} entries, fewer than rows + 1 = {rows + 1}")
+    total = ctypes.c_int64(0)
+    _check(load().spgemm_scan_counts_noalloc(row_ptr.data_ptr() if row_ptr.numel() else None, int(rows),
+                                             ctypes.byref(total), _stream(stream)), "spgemm_scan_counts_noalloc")
+    return total.value
 
 
 # ---- the whole product ----------------------------------------------------------------------

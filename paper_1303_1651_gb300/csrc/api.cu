@@ -121,6 +121,7 @@ const char* spgemm_error_string(int code) {
     case SPGEMM_ERR_STATE: return "calls out of order";
     case SPGEMM_ERR_UNSORTED: return "reserved: unsorted input";
     case SPGEMM_ERR_MISMATCH: return "structure changed between symbolic and numeric";
+    case SPGEMM_ERR_SCRATCH_LIMIT: return "size exceeds the fixed scratch of a no-allocation entry point";
     default: return "unknown status";
   }
 }

@@ -35,7 +35,7 @@ def test_every_declared_symbol_exported(lib):
 
 
 def test_error_strings(lib):
-    for code in range(10):
+    for code in range(11):
         s = binding.error_string(code)
         assert isinstance(s, str) and s
     assert binding.error_string(12345) == "unknown status"
@@ -78,6 +78,12 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.spgemm_symbolic(None, 0x1000, ctypes.byref(ctypes.c_int64()), None) == 7
     assert lib.spgemm_numeric(None, None, None, None, None, None) == 7
     assert lib.spgemm_free(None) == 0
+    # the no-workspace scan checks its arguments and its size limit before any CUDA call
+    total = ctypes.c_int64(-1)
+    assert lib.spgemm_scan_counts_noalloc(None, 10, ctypes.byref(total), None) == 1
+    assert lib.spgemm_scan_counts_noalloc(0x1000, -1, ctypes.byref(total), None) == 1
+    assert lib.spgemm_scan_counts_noalloc(0x1000, (1 << 26), ctypes.byref(total), None) == 10
+    assert total.value == -1
 
 
 def test_struct_sizes_match_header(lib):
