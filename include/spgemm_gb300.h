@@ -24,8 +24,11 @@
  *   - Rows of C come out sorted by column, without duplicates.
  *   - Rows of A and of B may be in any order and may repeat a column (repeated
  *     entries each contribute their products).
- *   - Each value of C is a sum of products a_rj * b_jx rounded one by one
- *     (no fused multiply-add).
+ *   - Each value of C is the FP64 sum of its products a_rj * b_jx, rounded to
+ *     nearest.  Short rows (the sort classes) add them in storage order with
+ *     fused multiply-adds, the first against +0.0.  Longer rows (the hash and
+ *     dense classes) add separately rounded products in no fixed order.  An
+ *     entry made of one product is exactly the rounded product in every class.
  *
  * Memory and ownership:
  *   - All matrix arrays and the workspace are DEVICE pointers owned by the
