@@ -10,32 +10,33 @@
 // One warp owns a tile of 32 consecutive rows; lane t owns row tile*32 + t,
 // whose u_t <= N products (N = 32 or 64, chosen per matrix from the longest
 // merge-class row) come from at most 8 entries of A.
-//   1. run table   -- lane t gathers its runs (A entry -> B row range).
-//   2. expand      -- the warp copies every product's column (and b_jx) into
-//                     shared memory with lane-parallel, coalesced cp.async copies,
-//                     the whole tile in flight at once.  Lanes walk the tile's
-//                     product space; a redux.or of run-start bits names each
-//                     lane's run.  Layout [j][t] with an XOR swizzle: conflict-free
-//                     for these writes (fixed t, consecutive j) and for the
-//                     per-lane reads below (fixed j).  Then each lane multiplies
-//                     its staged b_jx by a_rj, one multiply per product.
-//   3. sort        -- lane t loads keys (column << log2 N | product index) into
+//   1. run table   -- lane t gathers its runs (A entry -> B row range) and, from
+//                     them, the start mask of its runs and the B offset of each run.
+//   2. expand      -- the warp copies every product's column (and, in the staged
+//                     form, b_jx) into shared memory with lane-parallel, coalesced
+//                     cp.async copies, the whole tile in flight at once.  Lanes walk
+//                     the tile's product space 32 products at a time; a redux.or of
+//                     run-start bits names each lane's run.  Row t's products are
+//                     contiguous, one slot of skew per row.
+//   3. sort        -- lane t loads keys (column | run rank | product index) into
 //                     registers and runs a bitonic network.  Equal columns end up
-//                     adjacent, ordered by product index: the order of the
+//                     adjacent, in run order and then B order: the order of the
 //                     dense-accumulator loop.
 //   4. count       -- distinct columns of the row (symbolic result).
-//   5. reduce      -- sums each group of equal columns in that order, first
-//                     product stored and the rest added, and leaves the sum in the
-//                     slot of the group's last product (already read); the group's
-//                     key goes to the tile's flat output list.
+//   5. reduce      -- acc = fma(a_rj, b_jx, acc) along each group of equal columns
+//                     in that order, the first product against +0.0.
 //   6. place       -- numeric: C's row pointer is known.  Fused: the tile publishes
 //                     its entry count and finds its offset in C by a decoupled
 //                     look-back over the preceding tiles (the streaming append of
 //                     Section IV-B: one allocation sized by the multiplication
 //                     count, rows appended in order), then writes C's row pointers.
 //   7. write       -- consecutive lanes store consecutive entries of C.
+// Two forms of steps 5-7: the staged form keeps b_jx in shared memory, writes each
+// group's sum back there and stores C in a coalesced pass; the direct form reads
+// b_jx from B in the reduce (four positions' loads in flight at a time) and stores
+// each finished entry of C from there, so it needs less shared memory per warp.
 // Rows of B need not be sorted: the network orders everything.  Keys need
-// column < 2^26 - 1; wider matrices use the hash classes.
+// column < 2^23 - 1; wider matrices use the hash classes.
 #include "internal.h"
 
 namespace spg {
@@ -58,7 +59,8 @@ struct SortSmem {
   static constexpr size_t s_col = s_val + (SV ? 8 * SLOTS : 0);    // uint   [SLOTS]  columns, later output keys
   static constexpr size_t r_run = s_col + 4 * SLOTS;               // int2   [MAXR]   (first B entry, start << 8 | lane)
   static constexpr size_t s_bofs = r_run + 8 * MAXR;               // int    [8][32]  (DIRECT) B offset of a run rank
-  static constexpr size_t bytes = s_bofs + (DIRECT ? 4 * 8 * 32 : 0);  // s_a (double [8][32], a_rj by run rank
+  static constexpr size_t s_cfr = s_bofs + (DIRECT ? 4 * 8 * 32 : 0);  // int [N]  (N = 64) run holding product 32c
+  static constexpr size_t bytes = s_cfr + (N == 64 ? 4 * N : 0);   // s_a (double [8][32], a_rj by run rank
                                                                    // and lane) reuses r_run after the expand
   static_assert(8 * 8 * 32 <= 8 * MAXR, "a table must fit in the run table");
 };
@@ -152,6 +154,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
   int2* r_run = reinterpret_cast<int2*>(wb + L::r_run);
   double* s_a = reinterpret_cast<double*>(wb + L::r_run);
   int* s_bofs = reinterpret_cast<int*>(wb + L::s_bofs);
+  int* s_cfr = reinterpret_cast<int*>(wb + L::s_cfr);
   const DevCsr& A = g.A;
   const DevCsr& B = g.B;
 
@@ -195,13 +198,20 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
   const int pofs = warp_excl_scan(u, &P);
   const int rofs = warp_excl_scan(nz, &R);
   const int base = pofs + lane;            // this row's first staging slot
+  unsigned long long starts = 0;
+  unsigned nem = 0;
   {
-    int d = 0, q = rofs;
+    int d = 0, q = rofs, qq = 0;
 #pragma unroll
     for (int i = 0; i < MERGE_K; ++i) {
       if (len[i] > 0) {
         r_run[q] = make_int2(src[i], ((pofs + d) << 8) | lane);
-        ++q;
+        if (N == 64)   // chunks of 32 products whose first product lies in this run
+          for (int c = (pofs + d + 31) >> 5; (c << 5) < pofs + d + len[i]; ++c) s_cfr[c] = q;
+        if (d > 0) starts |= 1ull << d;                    // bit x: a nonempty run starts at product x
+        if (DIRECT) s_bofs[qq * 32 + lane] = src[i] - d;   // b of product index x of this run: B.val[bofs + x]
+        nem |= 1u << i;                                    // entry i of A has a nonempty run
+        ++q; ++qq;
         d += len[i];
       }
     }
@@ -210,7 +220,9 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
 
   // 2. expand: asynchronous global -> shared copies of the tile's columns and values, all in flight
   int e_cur = 0;
+#pragma unroll 2
   for (int cb = 0; cb < P; cb += 32) {
+    if (N == 64) e_cur = s_cfr[cb >> 5];   // independent of the previous chunk: chunks overlap
     const int cand = e_cur + 1 + lane;
     const int st = cand < R ? (r_run[cand].y >> 8) : KEY_NONE;
     const unsigned off = (unsigned)(st - cb);
@@ -225,7 +237,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
       cp_async4(s_col + d, B.col + sp);
       if (L::SV) cp_async8(s_val + d, B.val + sp);
     }
-    e_cur = __shfl_sync(FULL, e, 31);
+    if (N != 64) e_cur = __shfl_sync(FULL, e, 31);
   }
   cp_async_wait_all();
   __syncwarp();   // all copies landed; the run table is free
@@ -234,17 +246,13 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
   //    product's nonempty run: bits of `starts` mark where each nonempty run after the first begins.
   unsigned key[N];
   {
-    unsigned long long starts = 0;
-    int d = 0, q = 0;
+    int q = 0;
 #pragma unroll
     for (int i = 0; i < MERGE_K; ++i) {
-      if (len[i] > 0) {
-        if (d > 0) starts |= 1ull << d;
+      if ((nem >> i) & 1u) {
         if (V) s_a[q * 32 + lane] = av[i];
-        if (DIRECT) s_bofs[q * 32 + lane] = src[i] - d;   // b of product index x of this run: B.val[bofs + x]
         ++q;
       }
-      d += len[i];
     }
 #pragma unroll
     for (int j = 0; j < N; ++j) {
@@ -305,18 +313,30 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
     const int umax = __reduce_max_sync(FULL, u);
     int o = 0;
     double acc = 0.0;
+    // b_jx and a_rj of CH positions are loaded together, so that CH loads from B are in flight at
+    // once (the loads cannot move past the stores to C on their own).  Larger CH costs registers
+    // and with them warps.
+    constexpr int CH = 4 < N ? 4 : N;
+    double bb[CH], aa[CH];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
+      if ((j % CH) == 0 && j < umax) {
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+          const unsigned kq = key[j + q];
+          bb[q] = 0.0; aa[q] = 0.0;
+          if (j + q < umax && kq != PAD) {
+            const int idx = (int)(kq & (unsigned)(N - 1));
+            const int run = (int)((kq >> IB) & 7u);
+            bb[q] = __ldg(B.val + s_bofs[run * 32 + lane] + idx);
+            aa[q] = s_a[run * 32 + lane];
+          }
+        }
+      }
       if (j < umax) {
         const unsigned kj = key[j];
         const bool valid = kj != PAD;
-        const int idx = (int)(kj & (unsigned)(N - 1));
-        const int run = (int)((kj >> IB) & 7u);
-        double a = 0.0, b = 0.0;
-        if (valid) {
-          b = __ldg(B.val + s_bofs[run * 32 + lane] + idx);
-          a = s_a[run * 32 + lane];
-        }
+        const double a = aa[j % CH], b = bb[j % CH];
         const bool same = (j < 32) ? ((samemask_lo >> j) & 1u) : ((samemask_hi >> (j - 32)) & 1u);
         acc = __fma_rn(a, b, same ? acc : 0.0);
         bool next_same = false;
@@ -397,16 +417,35 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
   // 7. write the tile's entries: consecutive lanes on consecutive entries of C.
   if (TM >= 24 * __popc(__ballot_sync(FULL, mine && cnt > 0))) {
     // long rows: one row at a time
-    for (unsigned rows = __ballot_sync(FULL, mine && cnt > 0); rows; rows &= rows - 1) {
-      const int t = __ffs(rows) - 1;
-      const int ct = min(__shfl_sync(FULL, cnt, t), __shfl_sync(FULL, lim, t));
-      const int bt = __shfl_sync(FULL, base, t);
-      const long long gt = __shfl_sync(FULL, gstart, t);
-      for (int o = lane; o < ct; o += 32) {
-        const unsigned kf = s_col[bt + o];
-        const double vf = s_val[bt + (int)(kf & (unsigned)(N - 1))];
-        g.C_col[gt + o] = (int)(kf >> KB);
-        g.C_val[gt + o] = vf;
+    const int ctl = min(cnt, lim);
+    for (unsigned rows = __ballot_sync(FULL, mine && cnt > 0); rows;) {
+      const int t0 = __ffs(rows) - 1;
+      rows &= rows - 1;
+      const int t1 = rows ? __ffs(rows) - 1 : t0;
+      const bool two = rows != 0;
+      rows &= rows - 1;
+      const int ct0 = __shfl_sync(FULL, ctl, t0), ct1 = two ? __shfl_sync(FULL, ctl, t1) : 0;
+      const int bt0 = __shfl_sync(FULL, base, t0), bt1 = __shfl_sync(FULL, base, t1);
+      const long long gt0 = __shfl_sync(FULL, gstart, t0), gt1 = __shfl_sync(FULL, gstart, t1);
+      unsigned k0[N / 32], k1[N / 32];
+      double v0[N / 32], v1[N / 32];
+#pragma unroll
+      for (int h = 0; h < N / 32; ++h) {
+        const int o = lane + 32 * h;
+        k0[h] = o < ct0 ? s_col[bt0 + o] : 0u;
+        k1[h] = o < ct1 ? s_col[bt1 + o] : 0u;
+      }
+#pragma unroll
+      for (int h = 0; h < N / 32; ++h) {
+        const int o = lane + 32 * h;
+        if (o < ct0) v0[h] = s_val[bt0 + (int)(k0[h] & (unsigned)(N - 1))];
+        if (o < ct1) v1[h] = s_val[bt1 + (int)(k1[h] & (unsigned)(N - 1))];
+      }
+#pragma unroll
+      for (int h = 0; h < N / 32; ++h) {
+        const int o = lane + 32 * h;
+        if (o < ct0) { g.C_col[gt0 + o] = (int)(k0[h] >> KB); g.C_val[gt0 + o] = v0[h]; }
+        if (o < ct1) { g.C_col[gt1 + o] = (int)(k1[h] >> KB); g.C_val[gt1 + o] = v1[h]; }
       }
     }
   } else {
