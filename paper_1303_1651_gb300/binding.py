@@ -229,7 +229,7 @@ def spgemm_plan_set_events(plan: int, start=None, stop=None):
     """Record torch.cuda.Event objects (timing enabled) around the plan's compute kernels."""
     # torch creates the CUDA event on its first record(): record once so the handles exist
     for ev in (start, stop):
-        if ev is not None:
+        if ev is not None and not ev.cuda_event:
             ev.record()
     _check(load().spgemm_plan_set_events(plan, start.cuda_event if start is not None else None,
                                          stop.cuda_event if stop is not None else None), "spgemm_plan_set_events")

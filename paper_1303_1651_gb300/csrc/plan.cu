@@ -19,93 +19,136 @@ int num_sms() {
 // of row r (Section III); summed over rows it is the never-underestimating nnz
 // estimate of Section IV-B.  Each row gets the class of accumulator it will use.
 // ---------------------------------------------------------------------------
-constexpr int BIN_THREADS = 1024;
+constexpr int BIN_THREADS = 256;
+constexpr int BIN_ROWS = 2;   // rows per thread and step, their loads in flight together
+constexpr int BIN_EPR = 8;    // entries of A per row loaded in the first round
 
+// Products of entries [p0, a1) of A (the rare rows longer than BIN_EPR); -1 for an invalid entry
+__device__ __noinline__ long long bin_tail(const DevCsr A, const DevCsr B, int p0, int a1) {
+  long long u = 0;
+  for (int p = p0; p < a1; ++p) {
+    const int j = __ldg(A.col + p);
+    if ((unsigned)j >= (unsigned)B.rows) return -1;
+    const int len = __ldg(B.rp + j + 1) - __ldg(B.rp + j);
+    if (len < 0) return -1;
+    u += len;
+  }
+  return u;
+}
+
+// Grid-stride: each thread takes BIN_ROWS rows per step (rows r and r + G, G = threads in the
+// grid, so every load instruction of a warp stays coalesced), keeps its counters in registers
+// and adds them to the global counters once per block at the end.
 __global__ void __launch_bounds__(BIN_THREADS)
 k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l1, int* l2, int* l3, int* l4,
       Counters* __restrict__ ctr) {
   int* lists[NUM_CLS] = {l0, l1, l2, l3, l4};
-  const int r = blockIdx.x * BIN_THREADS + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  long long u = 0;
-  int c = -1;
+  const long long G = (long long)gridDim.x * BIN_THREADS;
+  long long F = 0, umax = 0;
+  int umax_merge = 0, cnt[NUM_CLS] = {0, 0, 0, 0, 0};
   bool bad = false;
-  if (r < A.rows) {
-    const int a0 = A.rp[r], a1 = A.rp[r + 1];
-    const int k = a1 - a0;
-    if (k < 0) bad = true;
-    // eight entries per round, all loads of a round in flight together
-    for (int p0 = a0; p0 < a1; p0 += 8) {
-      int j[8];
+  // the loop bound is warp-uniform (the warp's first row) so the ballots below see every lane
+  for (long long wb = (long long)blockIdx.x * BIN_THREADS + (threadIdx.x & ~31); wb < A.rows; wb += G * BIN_ROWS) {
+    int r[BIN_ROWS], a0[BIN_ROWS], a1[BIN_ROWS];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) j[i] = (p0 + i < a1) ? __ldg(A.col + p0 + i) : -1;
-      int lo[8], hi[8];
+    for (int q = 0; q < BIN_ROWS; ++q) {
+      const long long rl = wb + lane + q * G;
+      r[q] = rl < A.rows ? (int)rl : -1;
+      a0[q] = a1[q] = 0;
+      if (r[q] >= 0) { a0[q] = __ldg(A.rp + r[q]); a1[q] = __ldg(A.rp + r[q] + 1); }
+    }
+    int j[BIN_ROWS][BIN_EPR];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        lo[i] = hi[i] = 0;
-        if (j[i] >= 0) {
-          if ((unsigned)j[i] >= (unsigned)B.rows) { bad = true; continue; }
-          lo[i] = __ldg(B.rp + j[i]);
-          hi[i] = __ldg(B.rp + j[i] + 1);
-        } else if (p0 + i < a1) {
-          bad = true;   // negative column index
+    for (int q = 0; q < BIN_ROWS; ++q)
+#pragma unroll
+      for (int i = 0; i < BIN_EPR; ++i) j[q][i] = (a0[q] + i < a1[q]) ? __ldg(A.col + a0[q] + i) : -1;
+    int len[BIN_ROWS][BIN_EPR];
+#pragma unroll
+    for (int q = 0; q < BIN_ROWS; ++q)
+#pragma unroll
+      for (int i = 0; i < BIN_EPR; ++i) {
+        len[q][i] = 0;
+        if (a0[q] + i < a1[q]) {
+          if ((unsigned)j[q][i] >= (unsigned)B.rows) bad = true;   // also a negative column
+          else len[q][i] = __ldg(B.rp + j[q][i] + 1) - __ldg(B.rp + j[q][i]);
         }
       }
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int len = hi[i] - lo[i];
-        if (len < 0) bad = true; else u += len;
-      }
-    }
-    if (k <= lim.merge_k && u <= lim.m1_u) c = CLS_M1;
-    else if (k <= lim.merge_k && u <= lim.m2_u) c = CLS_M2;
-    else if (u <= lim.warp_u) c = CLS_W;
-    else if (u <= lim.block_u) c = CLS_B;
-    else c = CLS_G;
-    cls[r] = (uint8_t)c;
-  }
-  // warp-aggregated appends to the class lists (rare classes), block-aggregated counts
-  __shared__ int s_cnt[NUM_CLS];
-  __shared__ long long s_sum[BIN_THREADS / 32];
-  __shared__ long long s_max[BIN_THREADS / 32];
-  if (threadIdx.x < NUM_CLS) s_cnt[threadIdx.x] = 0;
-  __syncthreads();
+    for (int q = 0; q < BIN_ROWS; ++q) {
+      long long u = 0;
 #pragma unroll
-  for (int q = 0; q < NUM_CLS; ++q) {
-    const unsigned mask = __ballot_sync(FULL, c == q);
-    if (mask) {
-      if (lists[q]) {
-        const int leader = __ffs(mask) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&ctr->count[q], __popc(mask));
-        base = __shfl_sync(FULL, base, leader);
-        if (c == q) lists[q][base + __popc(mask & lanemask_lt())] = r;
-      } else if (lane == 0) {
-        atomicAdd(&s_cnt[q], __popc(mask));
+      for (int i = 0; i < BIN_EPR; ++i) {
+        if (len[q][i] < 0) bad = true; else u += len[q][i];
+      }
+      if (a1[q] - a0[q] > BIN_EPR) {
+        const long long t = bin_tail(A, B, a0[q] + BIN_EPR, a1[q]);
+        if (t < 0) bad = true; else u += t;
+      }
+      int c = -1;
+      if (r[q] >= 0) {
+        const int k = a1[q] - a0[q];
+        if (k < 0) bad = true;
+        if (k <= lim.merge_k && u <= lim.m1_u) c = CLS_M1;
+        else if (k <= lim.merge_k && u <= lim.m2_u) c = CLS_M2;
+        else if (u <= lim.warp_u) c = CLS_W;
+        else if (u <= lim.block_u) c = CLS_B;
+        else c = CLS_G;
+        cls[r[q]] = (uint8_t)c;
+        F += u;
+        umax = max(umax, u);
+        if (c == CLS_M1 || c == CLS_M2) umax_merge = max(umax_merge, (int)u);
+      }
+      // listed classes (the rare long rows): warp-aggregated appends; the others are only counted
+#pragma unroll
+      for (int cc = 0; cc < NUM_CLS; ++cc) {
+        if (lists[cc]) {
+          const unsigned mask = __ballot_sync(FULL, c == cc);
+          if (mask) {
+            const int leader = __ffs(mask) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&ctr->count[cc], __popc(mask));
+            base = __shfl_sync(FULL, base, leader);
+            if (c == cc) lists[cc][base + __popc(mask & lanemask_lt())] = r[q];
+          }
+        } else {
+          cnt[cc] += (c == cc);
+        }
       }
     }
   }
-  // block totals: F, the largest row, the largest merge-class row
-  long long ws = warp_sum_ll(u);
-  long long wm = u;
+  // block totals, then one global atomic of each per block
+  __shared__ long long s_F[BIN_THREADS / 32], s_umax[BIN_THREADS / 32];
+  __shared__ int s_um[BIN_THREADS / 32], s_cnt[BIN_THREADS / 32][NUM_CLS];
+  const int w = threadIdx.x >> 5;
+  const long long wF = warp_sum_ll(F);
+  long long wm = umax;
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) wm = max(wm, __shfl_xor_sync(FULL, wm, d));
-  const int um = __reduce_max_sync(FULL, (c == CLS_M1 || c == CLS_M2) ? (int)u : 0);
-  if (lane == 0 && um > 0) atomicMax(&ctr->max_u_merge, um);
-  const bool anybad = __any_sync(FULL, bad);
+  const int wum = __reduce_max_sync(FULL, umax_merge);
+  int wc[NUM_CLS];
+#pragma unroll
+  for (int cc = 0; cc < NUM_CLS; ++cc) wc[cc] = __reduce_add_sync(FULL, cnt[cc]);
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(&ctr->status, ST_INVALID);
   if (lane == 0) {
-    s_sum[threadIdx.x >> 5] = ws;
-    s_max[threadIdx.x >> 5] = wm;
-    if (anybad) atomicOr(&ctr->status, ST_INVALID);
+    s_F[w] = wF; s_umax[w] = wm; s_um[w] = wum;
+#pragma unroll
+    for (int cc = 0; cc < NUM_CLS; ++cc) s_cnt[w][cc] = wc[cc];
   }
   __syncthreads();
-  if (threadIdx.x < NUM_CLS && s_cnt[threadIdx.x]) atomicAdd(&ctr->count[threadIdx.x], s_cnt[threadIdx.x]);
   if (threadIdx.x == 0) {
     long long t = 0, mx = 0;
-    for (int w = 0; w < BIN_THREADS / 32; ++w) { t += s_sum[w]; mx = max(mx, s_max[w]); }
+    int mm = 0;
+    for (int i = 0; i < BIN_THREADS / 32; ++i) { t += s_F[i]; mx = max(mx, s_umax[i]); mm = max(mm, s_um[i]); }
     if (t) atomicAdd(&ctr->F, (unsigned long long)t);
+    if (mm > 0) atomicMax(&ctr->max_u_merge, mm);
     if (mx > INT_MAX) { atomicOr(&ctr->status, ST_OVERFLOW); mx = INT_MAX; }
-    atomicMax(&ctr->max_u, (int)mx);
+    if (mx > 0) atomicMax(&ctr->max_u, (int)mx);
+  }
+  if (threadIdx.x < NUM_CLS && !lists[threadIdx.x]) {
+    int t = 0;
+    for (int i = 0; i < BIN_THREADS / 32; ++i) t += s_cnt[i][threadIdx.x];
+    if (t) atomicAdd(&ctr->count[threadIdx.x], t);
   }
 }
 
@@ -114,7 +157,13 @@ void launch_bin(const DevCsr& A, const DevCsr& B, const Limits& lim_in, uint8_t*
   if (A.rows <= 0) return;
   Limits lim = lim_in;
   if (B.cols > merge_max_cols()) { lim.m1_u = -1; lim.m2_u = -1; }   // sort keys hold column << log2(N)
-  const int grid = (A.rows + BIN_THREADS - 1) / BIN_THREADS;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin, BIN_THREADS, 0);
+    if (per_sm < 1) per_sm = 1;
+  }
+  const long long need = ((long long)A.rows + (long long)BIN_THREADS * BIN_ROWS - 1) / ((long long)BIN_THREADS * BIN_ROWS);
+  const int grid = (int)std::max(1LL, std::min(need, (long long)num_sms() * per_sm));
   k_bin<<<grid, BIN_THREADS, 0, s>>>(A, B, lim, cls, lists[0], lists[1], lists[2], lists[3], lists[4], ctr);
 }
 

@@ -27,3 +27,11 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _library_built(request):
+    """GPU tests run the in-tree library: build it (a no-op when it is up to date) before the first."""
+    if gpu_available() and any("gpu" in item.keywords for item in request.session.items):
+        from paper_1303_1651_gb300 import build
+        build.build()
