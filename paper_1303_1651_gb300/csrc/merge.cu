@@ -473,6 +473,361 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
   }
 }
 
+// ---------------------------------------------------------------------------
+// Rows of up to 64 products, two lanes per row (staged form).  A warp owns 16 consecutive
+// rows; lane 2t+h holds half h of row t's products.  Each lane sorts its 32 keys, the pair
+// merges them (lane 1 reversed, one compare-exchange across the pair, then a bitonic merge in
+// each lane), so lane 2t holds the row's sorted positions 0..31 and lane 2t+1 positions
+// 32..63.  Each lane reduces its positions; a group of equal columns that crosses from lane 2t
+// into lane 2t+1 is finished by lane 2t+1 from lane 2t's partial sum, in the same order as a
+// single chain.  Per warp this needs half the shared memory of the one-lane-per-row form, so
+// twice as many warps fit on an SM.
+// ---------------------------------------------------------------------------
+template <int MODE>
+struct PairSmem {
+  static constexpr int ROWS = 16;
+  static constexpr int N = 64;
+  static constexpr int SLOTS = ROWS * N + ROWS;                    // one slot of skew per row
+  static constexpr bool V = MODE != MODE_SYM;
+  static constexpr size_t s_val = 0;                               // double [SLOTS]  b_jx, later group sums
+  static constexpr size_t s_col = s_val + (V ? 8 * SLOTS : 0);     // uint   [SLOTS]  columns, later output keys
+  static constexpr size_t r_run = s_col + 4 * SLOTS;               // int2   [ROWS * 8]; s_a (double [8][ROWS]) later
+  static constexpr size_t s_cfr = r_run + 8 * ROWS * MERGE_K;      // int    [32]  run holding product 32c
+  static constexpr size_t bytes = s_cfr + 4 * 32;
+};
+
+template <int N>
+__device__ __forceinline__ void bitonic_merge(unsigned (&k)[N]) {
+#pragma unroll
+  for (int stride = N >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int j = i ^ stride;
+      if (j > i) {
+        const unsigned a = k[i], b = k[j];
+        k[i] = min(a, b);
+        k[j] = max(a, b);
+      }
+    }
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void merge_tile_pair(const MergeArgs& g, int tile, unsigned char* wb) {
+  using L = PairSmem<MODE>;
+  constexpr bool V = L::V;
+  constexpr int H = 32;                     // sorted positions per lane
+  constexpr int IB = 6;                     // product-index bits of a key
+  constexpr int KB = IB + 3;                // key = col << KB | run << IB | index
+  constexpr unsigned PAD = 0xffffffffu;
+  const int lane = threadIdx.x & 31, t = lane >> 1, h = lane & 1;
+  double* s_val = reinterpret_cast<double*>(wb + L::s_val);
+  unsigned* s_col = reinterpret_cast<unsigned*>(wb + L::s_col);
+  int2* r_run = reinterpret_cast<int2*>(wb + L::r_run);
+  double* s_a = reinterpret_cast<double*>(wb + L::r_run);
+  int* s_cfr = reinterpret_cast<int*>(wb + L::s_cfr);
+  const DevCsr& A = g.A;
+  const DevCsr& B = g.B;
+
+  const int r = tile * L::ROWS + t;
+  const bool inrange = r < A.rows;
+  const int c = inrange ? (int)g.rowcls[r] : -1;
+  const bool mine = c == CLS_M1 || c == CLS_M2;
+  if (MODE != MODE_FUSED && !__any_sync(FULL, mine)) return;
+
+  // 1. run table: both lanes of a row read the same entries; lane h = 0 writes the tables
+  int a0 = 0, k = 0;
+  if (mine) { a0 = __ldg(A.rp + r); k = __ldg(A.rp + r + 1) - a0; }
+  int other = 0;
+  if (MODE == MODE_FUSED && inrange && !mine && h == 0) other = g.rp[r];
+  int gbeg = 0, gend = 0;
+  if (MODE == MODE_NUM && mine) { gbeg = __ldg(g.rp + r); gend = __ldg(g.rp + r + 1); }
+  int jcol[MERGE_K];
+  double av[MERGE_K];
+#pragma unroll
+  for (int i = 0; i < MERGE_K; ++i) {
+    jcol[i] = -1;
+    av[i] = 0.0;
+    if (i < k) {
+      jcol[i] = __ldg(A.col + a0 + i);
+      if (V) av[i] = __ldg(A.val + a0 + i);
+    }
+  }
+  int src[MERGE_K], len[MERGE_K];
+#pragma unroll
+  for (int i = 0; i < MERGE_K; ++i) {
+    src[i] = 0; len[i] = 0;
+    if (jcol[i] >= 0) {
+      src[i] = __ldg(B.rp + jcol[i]);
+      len[i] = __ldg(B.rp + jcol[i] + 1) - src[i];
+    }
+  }
+  int u = 0, nz = 0;
+#pragma unroll
+  for (int i = 0; i < MERGE_K; ++i) { u += len[i]; nz += len[i] > 0; }
+  int P, R;
+  const int pofs = __shfl_sync(FULL, warp_excl_scan(h == 0 ? u : 0, &P), lane & ~1);   // the row's, in both lanes
+  const int rofs = warp_excl_scan(h == 0 ? nz : 0, &R);   // used by lane 2t only
+  const int base = pofs + t;               // this row's first staging slot
+  unsigned long long starts = 0;           // bit x: a nonempty run starts at product x (x > 0)
+  unsigned nem = 0;                        // bit i: entry i of A has a nonempty run
+  {
+    int d = 0, q = rofs;
+#pragma unroll
+    for (int i = 0; i < MERGE_K; ++i) {
+      if (len[i] > 0) {
+        if (h == 0) {
+          r_run[q] = make_int2(src[i], ((pofs + d) << 8) | t);
+          for (int cc = (pofs + d + 31) >> 5; (cc << 5) < pofs + d + len[i]; ++cc) s_cfr[cc] = q;
+        }
+        if (d > 0) starts |= 1ull << d;
+        nem |= 1u << i;
+        ++q;
+        d += len[i];
+      }
+    }
+  }
+  __syncwarp();
+
+  // 2. expand: the tile's columns (and values) into shared memory, all copies in flight
+#pragma unroll 2
+  for (int cb = 0; cb < P; cb += 32) {
+    const int e_cur = s_cfr[cb >> 5];
+    const int cand = e_cur + 1 + lane;
+    const int st = cand < R ? (r_run[cand].y >> 8) : KEY_NONE;
+    const unsigned off = (unsigned)(st - cb);
+    const unsigned bit = off < 32u ? (1u << off) : 0u;
+    const unsigned M = __reduce_or_sync(FULL, bit);
+    const int e = e_cur + __popc(M & lanemask_le());
+    const int p = cb + lane;
+    if (p < P) {
+      const int2 rr = r_run[e];
+      const int sp = rr.x + (p - (rr.y >> 8));
+      const int d = p + (rr.y & 31);      // product p of row t lives at slot p + t
+      cp_async4(s_col + d, B.col + sp);
+      if (V) cp_async8(s_val + d, B.val + sp);
+    }
+  }
+  cp_async_wait_all();
+  __syncwarp();   // all copies landed; the run table is free
+
+  // 3. keys of this lane's half (products 32h .. 32h + 31), sort, then merge across the pair
+  unsigned key[H];
+  {
+    if (V && h == 0) {
+      int q = 0;
+#pragma unroll
+      for (int i = 0; i < MERGE_K; ++i) {
+        if ((nem >> i) & 1u) {
+          s_a[q * L::ROWS + t] = av[i];
+          ++q;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const int x = H * h + ((j + 16 * h) & (H - 1));   // lane 2t+1 rotated by 16: the pair reads different banks
+      const unsigned rj = (unsigned)__popcll(starts & ((2ull << x) - 1ull));
+      key[j] = (x < u) ? ((s_col[base + x] << KB) | (rj << IB) | (unsigned)x) : PAD;
+    }
+  }
+  __syncwarp();   // every lane has its keys: s_col may now be overwritten
+  bitonic_sort<H>(key);
+#pragma unroll
+  for (int i = 0; i < H / 2; ++i) {   // lane 2t+1: descending, so the pair forms one bitonic sequence
+    const unsigned x = key[i], y = key[H - 1 - i];
+    key[i] = h ? y : x;
+    key[H - 1 - i] = h ? x : y;
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const unsigned o = __shfl_xor_sync(FULL, key[i], 1);
+    key[i] = h ? max(key[i], o) : min(key[i], o);
+  }
+  bitonic_merge<H>(key);
+
+  // 4. distinct columns; bit 0 of lane 2t+1's mask: its first group continues lane 2t's last
+  unsigned samemask = 0;
+#pragma unroll
+  for (int j = 1; j < H; ++j) {
+    const bool same = (key[j] != PAD) && ((key[j] >> KB) == (key[j - 1] >> KB));
+    samemask |= same ? (1u << j) : 0u;
+  }
+  const unsigned prev_last = __shfl_xor_sync(FULL, key[H - 1], 1);
+  const bool cont0 = h == 1 && key[0] != PAD && (key[0] >> KB) == (prev_last >> KB);
+  samemask |= cont0 ? 1u : 0u;
+  const int nvalid = h == 0 ? min(u, H) : max(u - H, 0);
+  const int cnt_lane = nvalid - __popc(samemask);
+  const int cnt = cnt_lane + __shfl_xor_sync(FULL, cnt_lane, 1);   // the row's distinct columns
+  if (MODE == MODE_SYM) {
+    if (mine && h == 0) g.rp[r] = cnt;
+    return;
+  }
+  const int mycount = h == 0 ? (mine ? cnt : other) : 0;
+  int TA = 0;
+  const int oa = (MODE == MODE_FUSED) ? warp_excl_scan(mycount, &TA) : 0;
+  if (MODE == MODE_FUSED) tile_publish(g.tile_state, tile, TA);
+
+  // 5. reduce, pass 1: each lane's chains; a continued first group (cont0) is left for pass 2
+  const bool next_cont = __shfl_xor_sync(FULL, cont0 ? 1 : 0, 1) != 0 && h == 0;   // lane 2t: last group goes on
+  // lane 2t's entries come first; lane 2t+1 starts after them (and after the continued group)
+  const unsigned endmask = ~((samemask >> 1) | (next_cont ? 0x80000000u : 0u));   // bit j: position j ends a group
+  const unsigned validmask = nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u);
+  const int ends_lane = __popc(endmask & validmask);
+  const int ends_lo = __shfl_sync(FULL, ends_lane, lane & ~1);
+  int o = h == 0 ? 0 : ends_lo + (cont0 ? 1 : 0);
+  const int umax = __reduce_max_sync(FULL, nvalid);
+  double acc = 0.0;
+  {
+    bool first_open = cont0;   // lane 2t+1 inside the continued group
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      if (j < umax) {
+        const unsigned kj = key[j];
+        const bool valid = kj != PAD;
+        const int idx = (int)(kj & 63u);
+        const int run = (int)((kj >> IB) & 7u);
+        double a = 0.0, b = 0.0;
+        if (valid) {
+          b = s_val[base + idx];
+          a = s_a[run * L::ROWS + t];
+        }
+        const bool same = j > 0 && ((samemask >> j) & 1u);
+        acc = __fma_rn(a, b, same ? acc : 0.0);
+        if (valid && ((endmask >> j) & 1u)) {
+          if (!first_open) {
+            s_col[base + o] = kj;
+            s_val[base + idx] = acc;
+            ++o;
+          }
+          first_open = false;
+        }
+      }
+    }
+  }
+  // pass 2: lane 2t+1 finishes the continued group from lane 2t's partial sum (acc after its
+  // last position, which is valid whenever the group continues)
+  const double carry = __shfl_xor_sync(FULL, acc, 1);
+  const int glen = cont0 ? ((~samemask == 0u) ? H : (__ffs(~samemask) - 1)) : 0;   // positions 0 .. glen-1
+  const int gmax = __reduce_max_sync(FULL, glen);
+  if (gmax > 0) {
+    double acc2 = carry;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      if (j < gmax) {
+        if (j < glen) {
+          const unsigned kj = key[j];
+          const int idx = (int)(kj & 63u);
+          const int run = (int)((kj >> IB) & 7u);
+          acc2 = __fma_rn(s_a[run * L::ROWS + t], s_val[base + idx], acc2);
+          if (j == glen - 1) {
+            s_col[base + ends_lo] = kj;
+            s_val[base + idx] = acc2;
+          }
+        }
+      }
+    }
+  }
+
+  // 6. place the tile in C
+  const int oa_row = __shfl_sync(FULL, oa, lane & ~1);
+  long long gstart = 0;
+  int lim = INT_MAX;
+  if (MODE == MODE_NUM) {
+    gstart = gbeg;
+    lim = gend - gbeg;
+    if (mine && h == 0 && lim != cnt) atomicOr(&g.ctr->status, ST_MISMATCH);
+  } else {
+    const long long off = tile_lookback(g.tile_state, tile, TA, g.ctr);
+    gstart = off + oa_row;
+    if (inrange && h == 0) {
+      const int rowcount = mine ? cnt : other;
+      if (gstart + rowcount > INT_MAX) atomicOr(&g.ctr->status, ST_OVERFLOW);
+      g.rp[r] = (int)gstart;
+      if (r == A.rows - 1) {
+        g.rp[r + 1] = (int)(gstart + rowcount);
+        g.ctr->nnzC = gstart + rowcount;
+      }
+    }
+    if (off + TA > g.capacity) {
+      if (lane == 0) atomicOr(&g.ctr->status, ST_OVERFLOW);
+      return;
+    }
+  }
+  __syncwarp();
+
+  // 7. write: rows in lane order (h = 0 lanes), two rows per step, consecutive lanes on
+  //    consecutive entries of C
+  const int ctl = min(cnt, lim);
+  for (unsigned rows = __ballot_sync(FULL, h == 0 && mine && cnt > 0); rows;) {
+    const int t0 = __ffs(rows) - 1;
+    rows &= rows - 1;
+    const int t1 = rows ? __ffs(rows) - 1 : t0;
+    const bool two = rows != 0;
+    rows &= rows - 1;
+    const int ct0 = __shfl_sync(FULL, ctl, t0), ct1 = two ? __shfl_sync(FULL, ctl, t1) : 0;
+    const int bt0 = __shfl_sync(FULL, base, t0), bt1 = __shfl_sync(FULL, base, t1);
+    const long long gt0 = __shfl_sync(FULL, gstart, t0), gt1 = __shfl_sync(FULL, gstart, t1);
+    unsigned k0[2], k1[2];
+    double v0[2], v1[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int oo = lane + 32 * q;
+      k0[q] = oo < ct0 ? s_col[bt0 + oo] : 0u;
+      k1[q] = oo < ct1 ? s_col[bt1 + oo] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int oo = lane + 32 * q;
+      if (oo < ct0) v0[q] = s_val[bt0 + (int)(k0[q] & 63u)];
+      if (oo < ct1) v1[q] = s_val[bt1 + (int)(k1[q] & 63u)];
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int oo = lane + 32 * q;
+      if (oo < ct0) { g.C_col[gt0 + oo] = (int)(k0[q] >> KB); g.C_val[gt0 + oo] = v0[q]; }
+      if (oo < ct1) { g.C_col[gt1 + oo] = (int)(k1[q] >> KB); g.C_val[gt1 + oo] = v1[q]; }
+    }
+  }
+}
+
+// 16 warps of at most 128 registers: shared memory allows 17 per SM
+template <int MODE>
+__global__ void __launch_bounds__(32, 16)
+k_merge_pair(MergeArgs g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int ntiles = (g.A.rows + PairSmem<MODE>::ROWS - 1) / PairSmem<MODE>::ROWS;
+  if (MODE != MODE_FUSED) {
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      merge_tile_pair<MODE>(g, tile, smem);
+      __syncwarp();
+    }
+  } else {
+    while (true) {
+      int tile = 0;
+      if (lane == 0) tile = (int)atomicAdd(&g.ctr->ticket, 1u);
+      tile = __shfl_sync(FULL, tile, 0);
+      if (tile >= ntiles) break;
+      merge_tile_pair<MODE>(g, tile, smem);
+      __syncwarp();
+    }
+  }
+}
+
+template <int MODE>
+static void launch_merge_pair(const MergeArgs& g, cudaStream_t s) {
+  constexpr size_t bytes = PairSmem<MODE>::bytes;
+  auto kern = k_merge_pair<MODE>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  const int ntiles = (g.A.rows + PairSmem<MODE>::ROWS - 1) / PairSmem<MODE>::ROWS;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, bytes);
+  if (per_sm < 1) per_sm = 1;
+  const int blocks = std::max(1, std::min(ntiles, num_sms() * per_sm * (MODE == MODE_FUSED ? 1 : 4)));
+  kern<<<blocks, 32, bytes, s>>>(g);
+}
+
 template <int MODE, int N, int WARPS, bool DIRECT>
 __global__ void __launch_bounds__(WARPS * 32, 1)
 k_merge(MergeArgs g) {
@@ -519,7 +874,8 @@ static void launch_merge(const MergeArgs& g, cudaStream_t s) {
 
 int merge_max_cols() { return (1 << 23) - 2; }
 
-size_t fused_tile_state_bytes(int rows) { return (size_t)((rows + 31) / 32) * sizeof(unsigned long long); }
+// tiles of 32 rows, or of 16 in the two-lanes-per-row form
+size_t fused_tile_state_bytes(int rows) { return (size_t)((rows + 15) / 16) * sizeof(unsigned long long); }
 
 void launch_merge_symbolic(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* counts,
                            Counters* ctr, cudaStream_t s) {
@@ -537,7 +893,7 @@ void launch_merge_numeric(int wide, int values_mode, const DevCsr& A, const DevC
     else launch_merge<MODE_NUM, 64, 1, true>(g, s);
   } else {
     if (!wide) launch_merge<MODE_NUM, 32, 1>(g, s);
-    else launch_merge<MODE_NUM, 64, 1>(g, s);
+    else launch_merge_pair<MODE_NUM>(g, s);
   }
 }
 
@@ -551,7 +907,7 @@ void launch_merge_fused(int wide, int values_mode, const DevCsr& A, const DevCsr
     else launch_merge<MODE_FUSED, 64, 1, true>(g, s);
   } else {
     if (!wide) launch_merge<MODE_FUSED, 32, 1>(g, s);
-    else launch_merge<MODE_FUSED, 64, 1>(g, s);
+    else launch_merge_pair<MODE_FUSED>(g, s);
   }
 }
 
