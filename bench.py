@@ -318,7 +318,8 @@ def run_ours(args, rank, world, local_rank):
         num_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(p["ev0"], p["ev1"])]))
         cls = p["info"]["rows_per_class"]
         wide = p["info"]["max_row_products"] > 32 and cls["M2"] > 0
-        kern = "k_merge<fused," + ("64" if wide else "32") + ">"
+        # default options: 32-product tiles use the direct form, 64-product rows the two-lanes-per-row form
+        kern = "k_merge_pair<fused>" if wide else "k_merge<fused,32>"
         d = {"F": p["info"]["products"], "nnz_c": p["nnz"], "bytes_min": bmin, "compute_ms": num_ms,
              "compute_kernel": kern, "rows_per_class": cls,
              "compute_gbs": bmin / (num_ms * 1e-3) / 1e9,
