@@ -184,6 +184,39 @@ spgemm_status_t spgemm_compute_async(spgemm_plan_t plan, const double* A_val, co
                                      int32_t* C_row_ptr, int32_t* C_col, double* C_val, int64_t capacity,
                                      int64_t* nnz_c_device, void* stream);
 
+/* Pattern reuse: new values of A and B, the same structures, C's structure kept.
+ *
+ * The row-major loop of Section IV-A visits the products of a row in a fixed order (A's entries
+ * in storage order, each followed by its row of B in storage order), and the store of Section
+ * IV-B gives each column of the row a fixed position in C.  spgemm_replay_record stores, once,
+ * the position each product of the short rows lands on (the rows of the sort classes: at most
+ * 8 entries of A and 64 products, so one byte per product).  spgemm_replay then recomputes C's
+ * values as c[pos] = fma(a_rj, b_jx, c[pos]) in that loop order, without sorting or hashing.
+ * On these rows its results equal spgemm_numeric's bit for bit.  Longer rows run
+ * spgemm_numeric's own kernels, whose atomic sums have no fixed order (same tolerance).
+ *
+ * spgemm_replay_size: bytes of the position map, a device buffer the caller owns: 4 bytes per
+ * tile of 32 rows, rounded up to 256, then 32 * U bytes per tile, U the longest short row (at
+ * most 64 products; for the Laplacian^2 about F bytes in all).  Host only.
+ * Errors: STATE (no plan), INVALID. */
+spgemm_status_t spgemm_replay_size(spgemm_plan_t plan, size_t* bytes);
+
+/* Record the position map for C's current structure.  Needs the plan after spgemm_symbolic +
+ * spgemm_numeric, or after spgemm_compute.  C_col holds C's column indices (device).  map is
+ * device memory, 256-byte aligned, of at least spgemm_replay_size bytes, and is kept by the
+ * plan for spgemm_replay.  Enqueues on stream and synchronises it.  Errors: STATE, INVALID,
+ * ALLOC, OVERFLOW (the map would pass INT32_MAX bytes), MISMATCH (a product's column is
+ * not in its row of C: C_col is not this product's structure), CUDA. */
+spgemm_status_t spgemm_replay_record(spgemm_plan_t plan, const int32_t* C_col, void* map, size_t map_bytes,
+                                     void* stream);
+
+/* Recompute C's values from new values of A and B with the map recorded for this plan.  C_val
+ * (device, nnz(C)) is written; C_col (device) is rewritten, with the same indices, for the rows
+ * outside the sort classes.  Enqueues on stream; no synchronisation; repeatable.  Errors: STATE
+ * (no map recorded for this plan, or another map passed), INVALID, CUDA. */
+spgemm_status_t spgemm_replay(spgemm_plan_t plan, const double* A_val, const double* B_val, const void* map,
+                              int32_t* C_col, double* C_val, void* stream);
+
 /* Bytes of device workspace spgemm_backward needs to form dB: the transpose of A's structure (the
  * CSR -> CSC conversion of Section IV-A).  Errors: INVALID. */
 spgemm_status_t spgemm_backward_workspace_size(const spgemm_csr_t* A, const spgemm_csr_t* B, size_t* bytes);

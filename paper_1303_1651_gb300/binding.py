@@ -78,13 +78,17 @@ def load():
         lib.spgemm_plan_info.argtypes = [vp, P(spgemm_info_t)]
         lib.spgemm_free.argtypes = [vp]
         lib.spgemm_scan_counts_noalloc.argtypes = [vp, ctypes.c_int64, P(ctypes.c_int64), vp]
+        lib.spgemm_replay_size.argtypes = [vp, P(ctypes.c_size_t)]
+        lib.spgemm_replay_record.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
+        lib.spgemm_replay.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.spgemm_error_string.argtypes = [ctypes.c_int]
         lib.spgemm_error_string.restype = ctypes.c_char_p
         lib.spgemm_version.restype = ctypes.c_int32
         for name in ("spgemm_workspace_size", "spgemm_plan", "spgemm_symbolic", "spgemm_numeric",
                      "spgemm_compute", "spgemm_status", "spgemm_plan_info", "spgemm_free",
                      "spgemm_plan_set_events", "spgemm_compute_async", "spgemm_backward_workspace_size",
-                     "spgemm_backward", "spgemm_scan_counts_noalloc"):
+                     "spgemm_backward", "spgemm_scan_counts_noalloc", "spgemm_replay_size",
+                     "spgemm_replay_record", "spgemm_replay"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -240,6 +244,23 @@ def spgemm_free(plan: int):
         load().spgemm_free(plan)
 
 
+def spgemm_replay_size(plan: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().spgemm_replay_size(plan, ctypes.byref(n)), "spgemm_replay_size")
+    return int(n.value)
+
+
+def spgemm_replay_record(plan: int, C_col: torch.Tensor, map_buf: torch.Tensor, stream=None):
+    _check(load().spgemm_replay_record(plan, _ptr(C_col), map_buf.data_ptr(), map_buf.numel() * map_buf.element_size(),
+                                       _stream(stream)), "spgemm_replay_record")
+
+
+def spgemm_replay(plan: int, A_val: torch.Tensor, B_val: torch.Tensor, map_buf: torch.Tensor, C_col: torch.Tensor,
+                  C_val: torch.Tensor, stream=None):
+    _check(load().spgemm_replay(plan, _ptr(A_val), _ptr(B_val), map_buf.data_ptr(), _ptr(C_col), _ptr(C_val),
+                                _stream(stream)), "spgemm_replay")
+
+
 def spgemm_scan_counts_noalloc(row_ptr: torch.Tensor, rows: int | None = None, stream=None) -> int:
     """In place: per-row counts in row_ptr[:rows] -> row pointers in row_ptr[:rows + 1]; returns the
     total.  Uses the library's fixed scratch array, so nothing is allocated; calls must not overlap."""
@@ -285,6 +306,19 @@ class Product:
             C_val = torch.empty(self.nnz, dtype=torch.float64, device=dev)
         spgemm_numeric(self.plan, A_val, B_val, C_col, C_val, stream)
         return DeviceCSR(self.A.rows, self.B.cols, self.C_row_ptr, C_col, C_val)
+
+    def record(self, C: DeviceCSR, stream=None):
+        """Record the position map of C's structure (a result of numeric) for replay()."""
+        self.map = torch.empty(spgemm_replay_size(self.plan), dtype=torch.uint8, device=self.A.row_ptr.device)
+        spgemm_replay_record(self.plan, C.col_idx, self.map, stream)
+        self.C_col = C.col_idx
+
+    def replay(self, A_val, B_val, C_val=None, stream=None) -> DeviceCSR:
+        """C's values for new values of A and B, through the recorded map (same bits as numeric)."""
+        if C_val is None:
+            C_val = torch.empty(self.nnz, dtype=torch.float64, device=self.A.row_ptr.device)
+        spgemm_replay(self.plan, A_val, B_val, self.map, self.C_col, C_val, stream)
+        return DeviceCSR(self.A.rows, self.B.cols, self.C_row_ptr, self.C_col, C_val)
 
     def close(self):
         if getattr(self, "plan", None):

@@ -102,6 +102,7 @@ struct spgemm_plan_s {
   int32_t* C_col = nullptr;     // set by numeric / compute (the backward reads C's structure)
   bool slabs_clean = false;
   const void* transposed_ws = nullptr;   // backward workspace holding A's transpose, once built
+  const void* replay_map = nullptr;      // position map recorded for this plan's C, if any
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // optional, recorded around the compute kernels
 };
 
@@ -313,6 +314,56 @@ spgemm_status_t spgemm_compute_async(spgemm_plan_t p, const double* A_val, const
   const spgemm_status_t e = compute_enqueue(p, A_val, B_val, C_row_ptr, C_col, C_val, capacity, s);
   if (e != SPGEMM_OK) return e;
   if (nnz_c_device) cudaMemcpyAsync(nnz_c_device, &p->ctr->nnzC, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  if (cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_replay_size(spgemm_plan_t p, size_t* bytes) {
+  if (!p || p->state < 1) return SPGEMM_ERR_STATE;
+  if (!bytes) return SPGEMM_ERR_INVALID;
+  *bytes = replay_map_bytes(p->A.rows, p->h.max_u_merge);
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_replay_record(spgemm_plan_t p, const int32_t* C_col, void* map, size_t map_bytes,
+                                     void* stream) {
+  if (!p || p->state < 2 || !p->C_rp) return SPGEMM_ERR_STATE;
+  if (!map || ((uintptr_t)map % ALIGN) != 0 || (!C_col && p->h.nnzC > 0)) return SPGEMM_ERR_INVALID;
+  if (map_bytes < replay_map_bytes(p->A.rows, p->h.max_u_merge)) return SPGEMM_ERR_ALLOC;
+  cudaStream_t s = (cudaStream_t)stream;
+  p->replay_map = nullptr;
+  if (p->A.rows > 0)
+    launch_replay_record(p->A, p->B, p->ws + p->L.cls, p->C_rp, C_col, map,
+                         (unsigned long long*)(p->ws + p->L.scan), p->ctr, s);
+  cudaMemcpyAsync(&p->h, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  const spgemm_status_t st = status_from_bits(p->h.status);
+  if (st != SPGEMM_OK) return st;
+  p->replay_map = map;
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_replay(spgemm_plan_t p, const double* A_val, const double* B_val, const void* map,
+                              int32_t* C_col, double* C_val, void* stream) {
+  if (!p || p->state < 2 || !map || map != p->replay_map) return SPGEMM_ERR_STATE;
+  if ((!A_val && p->A.nnz > 0) || (!B_val && p->B.nnz > 0)) return SPGEMM_ERR_INVALID;
+  if ((!C_col || !C_val) && p->h.nnzC > 0) return SPGEMM_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevCsr A = p->A, B = p->B;
+  A.val = A_val;
+  B.val = B_val;
+  const Layout& L = p->L;
+  const int* cnt = p->h.count;
+  if (p->ev_start) cudaEventRecord(p->ev_start, s);
+  if (cnt[CLS_M1] + cnt[CLS_M2] > 0) launch_replay(p->h.max_u_merge > 32, A, B, p->ws + L.cls, p->C_rp, map, C_val, s);
+  if (cnt[CLS_W] > 0)
+    launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s);
+  if (cnt[CLS_B] > 0)
+    launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], p->C_rp, C_col, C_val, p->ctr, s);
+  if (cnt[CLS_G] > 0)
+    launch_dense_numeric(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs, p->C_rp,
+                         C_col, C_val, p->ctr, s);
+  if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
   if (cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
   return SPGEMM_OK;
 }

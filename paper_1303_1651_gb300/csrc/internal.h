@@ -57,4 +57,11 @@ int num_sms();
 // Largest B.cols the merge classes accept (their sort keys hold column << 6).
 int merge_max_cols();
 
+// Pattern reuse (replay.cu): a position map for the products of the sort-class rows.
+size_t replay_map_bytes(int rows, int max_u);
+void launch_replay_record(const DevCsr& A, const DevCsr& B, const uint8_t* cls, const int* C_rp, const int* C_col,
+                          void* map, unsigned long long* scan_state, Counters* ctr, cudaStream_t s);
+void launch_replay(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* cls, const int* C_rp, const void* map,
+                   double* C_val, cudaStream_t s);
+
 }  // namespace spg

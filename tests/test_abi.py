@@ -78,6 +78,10 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.spgemm_symbolic(None, 0x1000, ctypes.byref(ctypes.c_int64()), None) == 7
     assert lib.spgemm_numeric(None, None, None, None, None, None) == 7
     assert lib.spgemm_free(None) == 0
+    # pattern reuse needs a plan (and a recorded map)
+    assert lib.spgemm_replay_size(None, ctypes.byref(ctypes.c_size_t())) == 7
+    assert lib.spgemm_replay_record(None, None, 0x1000, 1 << 20, None) == 7
+    assert lib.spgemm_replay(None, None, None, 0x1000, None, None, None) == 7
     # the no-workspace scan checks its arguments and its size limit before any CUDA call
     total = ctypes.c_int64(-1)
     assert lib.spgemm_scan_counts_noalloc(None, 10, ctypes.byref(total), None) == 1
