@@ -196,7 +196,7 @@ spgemm_status_t spgemm_symbolic(spgemm_plan_t p, int32_t* C_row_ptr, int64_t* nn
   const int wide = p->h.max_u_merge > 32;
   if (cnt[CLS_M1] + cnt[CLS_M2] > 0) launch_merge_symbolic(wide, p->A, p->B, cls, C_row_ptr, p->ctr, s);
   if (cnt[CLS_W] > 0)
-    launch_hash_symbolic(CLS_W, p->A, p->B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s);
+    launch_hash_symbolic(CLS_W, p->A, p->B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s, p->h.max_u_w);
   if (cnt[CLS_B] > 0)
     launch_hash_symbolic(CLS_B, p->A, p->B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s);
   if (cnt[CLS_G] > 0)
@@ -230,7 +230,7 @@ spgemm_status_t spgemm_numeric(spgemm_plan_t p, const double* A_val, const doubl
   if (cnt[CLS_M1] + cnt[CLS_M2] > 0)
     launch_merge_numeric(wide, p->values_mode, A, B, cls, p->C_rp, C_col, C_val, p->ctr, s);
   if (cnt[CLS_W] > 0)
-    launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s);
+    launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s, p->h.max_u_w);
   if (cnt[CLS_B] > 0)
     launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], p->C_rp, C_col, C_val, p->ctr, s);
   if (cnt[CLS_G] > 0)
@@ -268,7 +268,7 @@ static spgemm_status_t compute_enqueue(spgemm_plan_t p, const double* A_val, con
     }
     if (p->ev_start) cudaEventRecord(p->ev_start, s);
     if (cnt[CLS_W] > 0)
-      launch_hash_symbolic(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s);
+      launch_hash_symbolic(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s, p->h.max_u_w);
     if (cnt[CLS_B] > 0)
       launch_hash_symbolic(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s);
     if (cnt[CLS_G] > 0)
@@ -278,7 +278,7 @@ static spgemm_status_t compute_enqueue(spgemm_plan_t p, const double* A_val, con
     launch_merge_fused(wide, p->values_mode, A, B, cls, C_row_ptr, C_col, C_val, capacity,
                        (unsigned long long*)(p->ws + L.fused), p->ctr, s);
     if (cnt[CLS_W] > 0)
-      launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, C_col, C_val, p->ctr, s);
+      launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, C_col, C_val, p->ctr, s, p->h.max_u_w);
     if (cnt[CLS_B] > 0)
       launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, C_col, C_val, p->ctr, s);
     if (cnt[CLS_G] > 0)
@@ -357,7 +357,7 @@ spgemm_status_t spgemm_replay(spgemm_plan_t p, const double* A_val, const double
   if (p->ev_start) cudaEventRecord(p->ev_start, s);
   if (cnt[CLS_M1] + cnt[CLS_M2] > 0) launch_replay(p->h.max_u_merge > 32, A, B, p->ws + L.cls, p->C_rp, map, C_val, s);
   if (cnt[CLS_W] > 0)
-    launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s);
+    launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s, p->h.max_u_w);
   if (cnt[CLS_B] > 0)
     launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], p->C_rp, C_col, C_val, p->ctr, s);
   if (cnt[CLS_G] > 0)

@@ -48,7 +48,8 @@ struct Counters {
   int count[NUM_CLS];        // rows per class
   int max_u;                 // largest row product count
   int max_u_merge;           // largest product count among merge-class rows
-  int pad[5];
+  int max_u_w;               // largest product count among class-W rows
+  int pad[4];
 };
 
 struct Limits {

@@ -196,8 +196,7 @@ k_hash_num(DevCsr A, DevCsr B, const int* __restrict__ list, int count, const in
 // scanning the bits.  Wider rows use a hash table sized to the row, compacted in place and sorted
 // by a bitonic network over the distinct columns only.
 // ---------------------------------------------------------------------------
-constexpr int WR_UMAX = 1024;
-constexpr int WR_TMAX = 2048;
+constexpr int WR_UMAX = 1024;   // the largest bound U of the W kernels
 constexpr int WR_RANGE = 65536;
 constexpr int WR_WARPS = 2;
 
@@ -283,25 +282,37 @@ __device__ __forceinline__ int warp_sort_rank(const int* s_col, const double* s_
   return total;
 }
 
-template <bool NUM>
+// Shared memory of one warp of the W kernel for rows of at most U products.  Every piece scales
+// with U, so the rows of a matrix get the smallest footprint that holds its longest W row (and
+// with it the most warps per SM).  Region, per mode (NUM / symbolic):
+//   bit vector: bits uint[RW] @0, rank ushort[RW], sums double[U] (NUM)  -- RW = min(4U, WR_RANGE/32)
+//   register sort: columns int[U] @0, sums double[U] (NUM only)
+//   hash: vals double[2U] @0, keys int[2U] (NUM); keys int[2U] @0 (symbolic)
+template <bool NUM, int U>
 struct WarpRowSmem {
-  static constexpr size_t s_val = 0;                                  // double [WR_UMAX] products
-  static constexpr size_t s_col = s_val + (NUM ? 8 * WR_UMAX : 0);    // int    [WR_UMAX] columns
-  static constexpr size_t region = s_col + 4 * WR_UMAX;
-  // bit-vector mode: bits uint[WR_RANGE/32] @0, rank ushort[WR_RANGE/32] @8192, sums double[WR_UMAX] @12288
-  // hash mode:       vals double[WR_TMAX] @0, keys int[WR_TMAX] @16384 (NUM); keys @0 (symbolic)
-  static constexpr size_t region_bytes = NUM ? 24576 : 8192;
-  static constexpr size_t bytes = region + region_bytes;
+  static constexpr int RW = (4 * U < WR_RANGE / 32) ? 4 * U : WR_RANGE / 32;
+  static constexpr int TMAX = 2 * U;
+  static constexpr size_t s_val = 0;                                  // double [U] products
+  static constexpr size_t s_col = s_val + (NUM ? 8 * U : 0);          // int    [U] columns
+  static constexpr size_t region = s_col + 4 * U;
+  static constexpr size_t bv_rank = 4 * RW;
+  static constexpr size_t bv_sums = (6 * RW + 7) / 8 * 8;
+  static constexpr size_t rs_sums = 4 * U;
+  static constexpr size_t h_keys = NUM ? 8 * TMAX : 0;
+  static constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+  static constexpr size_t region_bytes =
+      NUM ? cmax(cmax(bv_sums + 8 * U, rs_sums + 8 * U), h_keys + 4 * TMAX) : cmax(4 * RW, 4 * TMAX);
+  static constexpr size_t bytes = (region + region_bytes + 15) / 16 * 16;
 };
 
 __device__ __forceinline__ int warp_min_i(int v) { return __reduce_min_sync(FULL, v); }
 __device__ __forceinline__ int warp_max_i(int v) { return __reduce_max_sync(FULL, v); }
 
-template <bool NUM>
+template <bool NUM, int U>
 __global__ void __launch_bounds__(WR_WARPS * 32, 1)
 k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __restrict__ rp,
            int* __restrict__ C_col, double* __restrict__ C_val, Counters* __restrict__ ctr) {
-  using L = WarpRowSmem<NUM>;
+  using L = WarpRowSmem<NUM, U>;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* wb = smem + (size_t)warp * L::bytes;
@@ -326,7 +337,7 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
       }
       int tot;
       const int off = warp_excl_scan(len, &tot);
-      if (u + tot > WR_UMAX) { over = true; break; }   // class limits make this unreachable
+      if (u + tot > U) { over = true; break; }   // the launch picks U >= every W row: unreachable
       for (int cb = 0; cb < tot; cb += 32) {
         const int q = cb + lane;
         int t = 0;   // last run whose offset is <= q (empty runs share the next run's offset)
@@ -361,15 +372,19 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
     // Choice of ordering (the "Combined" idea of Section IV-B): the bit vector when the column
     // range is small next to the row (at most 4u words), a register sort when the keys fit 32
     // bits, a hash table otherwise.
-    const bool bitvec = range <= WR_RANGE && (range >> 5) <= 4 * (long long)u;
+    const bool bitvec = range <= WR_RANGE && ((range + 31) >> 5) <= 4 * (long long)u;   // words <= 4u <= RW
     const bool regsort = !bitvec && range < (1 << 22);
     if (u > 0 && regsort) {
-      int* outc = reinterpret_cast<int*>(reg + 8192);
-      double* sums = reinterpret_cast<double*>(reg + 12288);
+      int* outc = reinterpret_cast<int*>(reg);
+      double* sums = reinterpret_cast<double*>(reg + L::rs_sums);
       if (u <= 128) cnt = warp_sort_rank<4, NUM>(s_col, s_val, u, mn, outc, sums);
-      else if (u <= 256) cnt = warp_sort_rank<8, NUM>(s_col, s_val, u, mn, outc, sums);
-      else if (u <= 512) cnt = warp_sort_rank<16, NUM>(s_col, s_val, u, mn, outc, sums);
-      else cnt = warp_sort_rank<32, NUM>(s_col, s_val, u, mn, outc, sums);
+      else if constexpr (U >= 256) {
+        if (u <= 256) cnt = warp_sort_rank<8, NUM>(s_col, s_val, u, mn, outc, sums);
+        else if constexpr (U >= 512) {
+          if (u <= 512) cnt = warp_sort_rank<16, NUM>(s_col, s_val, u, mn, outc, sums);
+          else cnt = warp_sort_rank<32, NUM>(s_col, s_val, u, mn, outc, sums);
+        }
+      }
       if (NUM) {
         if (lane == 0 && g1 - g0 != cnt) atomicOr(&ctr->status, ST_MISMATCH);
         for (int q = lane; q < cnt && g0 + q < g1; q += 32) {
@@ -380,7 +395,7 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
     } else if (u > 0 && bitvec) {
       // 2a. bit vector over [mn, mx]
       unsigned* bits = reinterpret_cast<unsigned*>(reg);
-      unsigned short* rank = reinterpret_cast<unsigned short*>(reg + 8192);
+      unsigned short* rank = reinterpret_cast<unsigned short*>(reg + L::bv_rank);
       const int W = (int)((range + 31) >> 5);
       for (int w = lane; w < W; w += 32) bits[w] = 0u;
       __syncwarp();
@@ -400,7 +415,7 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
       }
       cnt = base;
       if (NUM) {
-        double* sums = reinterpret_cast<double*>(reg + 12288);
+        double* sums = reinterpret_cast<double*>(reg + L::bv_sums);
         for (int q = lane; q < cnt; q += 32) sums[q] = 0.0;
         __syncwarp();
         for (int q = lane; q < u; q += 32) {
@@ -431,7 +446,7 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
       int logT = 6;
       while ((1 << logT) < 2 * u) ++logT;
       const int T = 1 << logT;
-      int* keys = reinterpret_cast<int*>(reg + (NUM ? 16384 : 0));
+      int* keys = reinterpret_cast<int*>(reg + L::h_keys);
       double* vals = reinterpret_cast<double*>(reg);
       for (int i = lane; i < T; i += 32) { keys[i] = KEY_NONE; if (NUM) vals[i] = 0.0; }
       __syncwarp();
@@ -495,17 +510,26 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
   }
 }
 
-template <bool NUM>
-static void launch_warp_row(const DevCsr& A, const DevCsr& B, const int* list, int count, int* rp, int* C_col,
-                            double* C_val, Counters* ctr, cudaStream_t s) {
-  if (count <= 0) return;
-  constexpr size_t bytes = (size_t)WR_WARPS * WarpRowSmem<NUM>::bytes;
-  auto kern = k_warp_row<NUM>;
+template <bool NUM, int U>
+static void launch_warp_row_u(const DevCsr& A, const DevCsr& B, const int* list, int count, int* rp, int* C_col,
+                              double* C_val, Counters* ctr, cudaStream_t s) {
+  constexpr size_t bytes = (size_t)WR_WARPS * WarpRowSmem<NUM, U>::bytes;
+  auto kern = k_warp_row<NUM, U>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WR_WARPS * 32, bytes);
   const int blocks = std::max(1, std::min((count + WR_WARPS - 1) / WR_WARPS, num_sms() * std::max(per_sm, 1)));
   kern<<<blocks, WR_WARPS * 32, bytes, s>>>(A, B, list, count, rp, C_col, C_val, ctr);
+}
+
+// umax: the longest W row (products); the smallest bound U >= umax is launched
+template <bool NUM>
+static void launch_warp_row(const DevCsr& A, const DevCsr& B, const int* list, int count, int umax, int* rp,
+                            int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
+  if (count <= 0) return;
+  if (umax <= 128) launch_warp_row_u<NUM, 128>(A, B, list, count, rp, C_col, C_val, ctr, s);
+  else if (umax <= 256) launch_warp_row_u<NUM, 256>(A, B, list, count, rp, C_col, C_val, ctr, s);
+  else launch_warp_row_u<NUM, WR_UMAX>(A, B, list, count, rp, C_col, C_val, ctr, s);
 }
 
 template <int GROUP, int LOG2T, int GPB, bool NUM>
@@ -531,14 +555,14 @@ static void launch_hash(const DevCsr& A, const DevCsr& B, const int* list, int c
 }
 
 void launch_hash_symbolic(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts,
-                          Counters* ctr, cudaStream_t s) {
-  if (cls == CLS_W) launch_warp_row<false>(A, B, list, count, counts, nullptr, nullptr, ctr, s);
+                          Counters* ctr, cudaStream_t s, int umax) {
+  if (cls == CLS_W) launch_warp_row<false>(A, B, list, count, umax, counts, nullptr, nullptr, ctr, s);
   else launch_hash<512, 13, 1, false>(A, B, list, count, counts, nullptr, nullptr, nullptr, ctr, s);
 }
 
 void launch_hash_numeric(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, const int* rp,
-                         int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
-  if (cls == CLS_W) launch_warp_row<true>(A, B, list, count, const_cast<int*>(rp), C_col, C_val, ctr, s);
+                         int* C_col, double* C_val, Counters* ctr, cudaStream_t s, int umax) {
+  if (cls == CLS_W) launch_warp_row<true>(A, B, list, count, umax, const_cast<int*>(rp), C_col, C_val, ctr, s);
   else launch_hash<512, 13, 1, true>(A, B, list, count, nullptr, rp, C_col, C_val, ctr, s);
 }
 

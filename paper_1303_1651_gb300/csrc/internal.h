@@ -31,11 +31,12 @@ void launch_merge_fused(int wide, int values_mode, const DevCsr& A, const DevCsr
                         cudaStream_t s);
 size_t fused_tile_state_bytes(int rows);
 
-// a2/a4, hash classes W (warp per row) and B (block per row), rows from a list.
+// a2/a4, hash classes W (warp per row) and B (block per row), rows from a list.  umax: the longest
+// W row's products (sizes the W kernel's shared memory); unused for class B.
 void launch_hash_symbolic(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts,
-                          Counters* ctr, cudaStream_t s);
+                          Counters* ctr, cudaStream_t s, int umax = 1024);
 void launch_hash_numeric(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, const int* rp,
-                         int* C_col, double* C_val, Counters* ctr, cudaStream_t s);
+                         int* C_col, double* C_val, Counters* ctr, cudaStream_t s, int umax = 1024);
 
 // a2/a4, class G: dense accumulator slabs in global memory (one slab per CTA).
 size_t dense_slab_bytes(int ncols);
