@@ -34,7 +34,8 @@
 // Two forms of steps 5-7: the staged form keeps b_jx in shared memory, writes each
 // group's sum back there and stores C in a coalesced pass; the direct form reads
 // b_jx from B in the reduce (four positions' loads in flight at a time) and stores
-// each finished entry of C from there, so it needs less shared memory per warp.
+// each finished entry of C from there; it also reads the columns straight from B when it
+// builds the keys (no expand), so it needs only the run tables in shared memory.
 // Rows of B need not be sorted: the network orders everything.  Keys need
 // column < 2^23 - 1; wider matrices use the hash classes.
 #include "internal.h"
@@ -57,7 +58,8 @@ struct SortSmem {
   static constexpr bool SV = V && !DIRECT;                          // values staged
   static constexpr size_t s_val = 0;                               // double [SLOTS]  b_jx, later group sums
   static constexpr size_t s_col = s_val + (SV ? 8 * SLOTS : 0);    // uint   [SLOTS]  columns, later output keys
-  static constexpr size_t r_run = s_col + 4 * SLOTS;               // int2   [MAXR]   (first B entry, start << 8 | lane)
+  static constexpr size_t r_run = s_col + (DIRECT ? 0 : 4 * SLOTS);  // int2   [MAXR]   (first B entry, start << 8 | lane);
+                                                                     // the direct form stages no columns
   static constexpr size_t s_bofs = r_run + 8 * MAXR;               // int    [8][32]  (DIRECT) B offset of a run rank
   static constexpr size_t s_cfr = s_bofs + (DIRECT ? 4 * 8 * 32 : 0);  // int [N]  (N = 64) run holding product 32c
   static constexpr size_t bytes = s_cfr + (N == 64 ? 4 * N : 0);   // s_a (double [8][32], a_rj by run rank
@@ -205,9 +207,13 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
 #pragma unroll
     for (int i = 0; i < MERGE_K; ++i) {
       if (len[i] > 0) {
-        r_run[q] = make_int2(src[i], ((pofs + d) << 8) | lane);
-        if (N == 64)   // chunks of 32 products whose first product lies in this run
-          for (int c = (pofs + d + 31) >> 5; (c << 5) < pofs + d + len[i]; ++c) s_cfr[c] = q;
+        if (!DIRECT) {
+          r_run[q] = make_int2(src[i], ((pofs + d) << 8) | lane);
+          if (N == 64)   // chunks of 32 products whose first product lies in this run
+            for (int c = (pofs + d + 31) >> 5; (c << 5) < pofs + d + len[i]; ++c) s_cfr[c] = q;
+        } else if (V) {
+          s_a[qq * 32 + lane] = av[i];
+        }
         if (d > 0) starts |= 1ull << d;                    // bit x: a nonempty run starts at product x
         if (DIRECT) s_bofs[qq * 32 + lane] = src[i] - d;   // b of product index x of this run: B.val[bofs + x]
         nem |= 1u << i;                                    // entry i of A has a nonempty run
@@ -219,27 +225,29 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
   __syncwarp();
 
   // 2. expand: asynchronous global -> shared copies of the tile's columns and values, all in flight
-  int e_cur = 0;
+  if constexpr (!DIRECT) {   // the direct form reads the columns from B when it builds the keys
+    int e_cur = 0;
 #pragma unroll 2
-  for (int cb = 0; cb < P; cb += 32) {
-    if (N == 64) e_cur = s_cfr[cb >> 5];   // independent of the previous chunk: chunks overlap
-    const int cand = e_cur + 1 + lane;
-    const int st = cand < R ? (r_run[cand].y >> 8) : KEY_NONE;
-    const unsigned off = (unsigned)(st - cb);
-    const unsigned bit = off < 32u ? (1u << off) : 0u;
-    const unsigned M = __reduce_or_sync(FULL, bit);
-    const int e = e_cur + __popc(M & lanemask_le());
-    const int p = cb + lane;
-    if (p < P) {
-      const int2 rr = r_run[e];
-      const int sp = rr.x + (p - (rr.y >> 8));
-      const int d = p + (rr.y & 31);      // product p of row t lives at slot p + t
-      cp_async4(s_col + d, B.col + sp);
-      if (L::SV) cp_async8(s_val + d, B.val + sp);
+    for (int cb = 0; cb < P; cb += 32) {
+      if (N == 64) e_cur = s_cfr[cb >> 5];   // independent of the previous chunk: chunks overlap
+      const int cand = e_cur + 1 + lane;
+      const int st = cand < R ? (r_run[cand].y >> 8) : KEY_NONE;
+      const unsigned off = (unsigned)(st - cb);
+      const unsigned bit = off < 32u ? (1u << off) : 0u;
+      const unsigned M = __reduce_or_sync(FULL, bit);
+      const int e = e_cur + __popc(M & lanemask_le());
+      const int p = cb + lane;
+      if (p < P) {
+        const int2 rr = r_run[e];
+        const int sp = rr.x + (p - (rr.y >> 8));
+        const int d = p + (rr.y & 31);      // product p of row t lives at slot p + t
+        cp_async4(s_col + d, B.col + sp);
+        if (L::SV) cp_async8(s_val + d, B.val + sp);
+      }
+      if (N != 64) e_cur = __shfl_sync(FULL, e, 31);
     }
-    if (N != 64) e_cur = __shfl_sync(FULL, e, 31);
+    cp_async_wait_all();
   }
-  cp_async_wait_all();
   __syncwarp();   // all copies landed; the run table is free
 
   // 3. sort this lane's products by (column, run, index).  The run field is the rank of the
@@ -250,14 +258,18 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
 #pragma unroll
     for (int i = 0; i < MERGE_K; ++i) {
       if ((nem >> i) & 1u) {
-        if (V) s_a[q * 32 + lane] = av[i];
+        if (V && !DIRECT) s_a[q * 32 + lane] = av[i];
         ++q;
       }
     }
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       const unsigned rj = (unsigned)__popcll(starts & ((2ull << j) - 1ull));
-      key[j] = (j < u) ? ((s_col[base + j] << KB) | (rj << IB) | (unsigned)j) : PAD;
+      if constexpr (DIRECT)   // column straight from B: all N loads of the lane in flight together
+        key[j] = (j < u) ? (((unsigned)__ldg(B.col + s_bofs[rj * 32 + lane] + j) << KB) | (rj << IB) | (unsigned)j)
+                         : PAD;
+      else
+        key[j] = (j < u) ? ((s_col[base + j] << KB) | (rj << IB) | (unsigned)j) : PAD;
     }
   }
   __syncwarp();   // every lane has its keys: s_col may now be overwritten
@@ -828,8 +840,10 @@ static void launch_merge_pair(const MergeArgs& g, cudaStream_t s) {
   kern<<<blocks, 32, bytes, s>>>(g);
 }
 
+// The fused direct form with 32-product tiles runs best with 28 warps of at most 72 registers
+// (a few spill to L1); the other forms keep their natural register counts.
 template <int MODE, int N, int WARPS, bool DIRECT>
-__global__ void __launch_bounds__(WARPS * 32, 1)
+__global__ void __launch_bounds__(WARPS * 32, (N == 32 && DIRECT && MODE == MODE_FUSED) ? 28 : 1)
 k_merge(MergeArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
