@@ -241,7 +241,7 @@ def run_numeric_only(args, prods, dev, stream, binding, torch):
 
 def run_ours(args, rank, world, local_rank):
     import torch
-    from paper_1303_1651_gb300 import binding, build
+    from paper_1303_1651_gb300 import binding, build, ranks
     build.build()
     binding.load()
     torch.cuda.set_device(local_rank)
@@ -322,11 +322,7 @@ def run_ours(args, rank, world, local_rank):
             step(record=True)
         t1.record(stream)
         barrier()
-    ms = t0.elapsed_time(t1) / args.steps
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = ranks.max_over_ranks(t0.elapsed_time(t1) / args.steps, dist, dev)
 
     # the three-call path (plan / symbolic / numeric) on the same inputs, for comparison
     for _ in range(2):
@@ -382,7 +378,7 @@ def run_ours(args, rank, world, local_rank):
         launches_per_step += 1 + 1 + 2 * others   # bin, fused merge pass, symbolic + numeric per other class
 
     # end to end through the C ABI from pinned host buffers
-    e2e = run_e2e(args, prods, dev, stream, binding, torch, world)
+    e2e = run_e2e(args, prods, dev, stream, binding, torch, world, dist)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -415,7 +411,7 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def run_e2e(args, prods, dev, stream, binding, torch, world):
+def run_e2e(args, prods, dev, stream, binding, torch, world, dist=None):
     """Same metric through the C ABI with host buffers: H2D of A, B and D2H of C inside the timed region."""
     host = []
     h2d = d2h = 0
@@ -487,7 +483,8 @@ def run_e2e(args, prods, dev, stream, binding, torch, world):
     for _ in range(steps):
         e2e_step()
     torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / steps
+    from paper_1303_1651_gb300 import ranks
+    dt = ranks.max_over_ranks((time.perf_counter() - t0) / steps, dist, dev)
     F_total = sum(p["info"]["products"] for p in prods)
     return {"value": world * 2 * F_total / dt / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": steps}

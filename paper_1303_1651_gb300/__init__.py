@@ -10,12 +10,16 @@ Submodules:
   synth    -- seeded synthetic inputs (FD 5-point Laplacian, random k per row, batches)
   roofline -- bytes/flops accounting of the product and the paper's balance model
   build    -- nvcc build of the library
+  autograd -- torch.autograd function over the product (values of A and B)
+  batched  -- many independent products as one block-diagonal product, replayed as a CUDA graph
+  tune     -- per-workload choice of row-class options
+  ranks    -- host-side helpers for one process per GPU (max over ranks, contiguous shards)
 """
 __version__ = "1.0.0"
 
 
 def __getattr__(name):
     import importlib
-    if name in ("binding", "synth", "build", "roofline", "autograd", "batched", "tune"):
+    if name in ("binding", "synth", "build", "roofline", "autograd", "batched", "tune", "ranks"):
         return importlib.import_module(f".{name}", __name__)
     raise AttributeError(name)
