@@ -35,7 +35,10 @@
  *     caller, who must keep them alive and unchanged until the last call that
  *     uses them has completed on its stream.
  *   - The library allocates no device memory.  spgemm_plan allocates the small
- *     host-side plan object, which spgemm_free releases.
+ *     host-side plan object, which spgemm_free releases.  Once per process, on the
+ *     first spgemm_plan, it also allocates an 18 KB pinned host buffer: each live plan
+ *     reads its counters back through one slot of it.  Plans beyond its 256 slots
+ *     use their own pageable copy.
  *   - A plan is not thread-safe.  Use it from one host thread and on one stream
  *     at a time.
  *

@@ -2,7 +2,9 @@
 // See include/spgemm_gb300.h for the contract of every entry point.
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "internal.h"
 #include "spgemm_gb300.h"
@@ -88,6 +90,44 @@ __global__ void k_validate(DevCsr M, Counters* ctr) {
 }
 }  // namespace spg
 
+namespace {
+
+// Counters are read back to the host after every synchronising call.  Through pinned memory
+// that is one DMA; through pageable memory the driver stages the copy.  A small pinned buffer,
+// allocated once per process on first use, gives each live plan a slot while slots last (plans
+// beyond that read into their own pageable copy).
+constexpr int PINNED_SLOTS = 256;
+std::mutex g_pin_mu;
+Counters* g_pin_base = nullptr;
+bool g_pin_tried = false;
+std::vector<int> g_pin_free;
+
+Counters* pinned_take() {
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  if (!g_pin_tried) {
+    g_pin_tried = true;
+    void* b = nullptr;
+    if (cudaHostAlloc(&b, PINNED_SLOTS * sizeof(Counters), cudaHostAllocPortable) == cudaSuccess) {
+      g_pin_base = (Counters*)b;
+      for (int i = PINNED_SLOTS - 1; i >= 0; --i) g_pin_free.push_back(i);
+    } else {
+      cudaGetLastError();   // no pinned buffer: every plan reads into pageable memory
+    }
+  }
+  if (!g_pin_base || g_pin_free.empty()) return nullptr;
+  const int i = g_pin_free.back();
+  g_pin_free.pop_back();
+  return g_pin_base + i;
+}
+
+void pinned_give(Counters* c) {
+  if (!c) return;
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  g_pin_free.push_back((int)(c - g_pin_base));
+}
+
+}  // namespace
+
 struct spgemm_plan_s {
   DevCsr A{}, B{};
   Limits lim{};
@@ -104,7 +144,21 @@ struct spgemm_plan_s {
   const void* transposed_ws = nullptr;   // backward workspace holding A's transpose, once built
   const void* replay_map = nullptr;      // position map recorded for this plan's C, if any
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // optional, recorded around the compute kernels
+  Counters* pinned = nullptr;   // this plan's slot of the pinned read-back buffer, if it got one
+  ~spgemm_plan_s() { pinned_give(pinned); }
 };
+
+namespace {
+// Read the device counters into p->h: enqueue the copy, synchronise the stream.
+cudaError_t read_counters(spgemm_plan_s* p, cudaStream_t s) {
+  Counters* dst = p->pinned ? p->pinned : &p->h;
+  cudaMemcpyAsync(dst, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess && p->pinned) p->h = *p->pinned;
+  return e;
+}
+}  // namespace
 
 extern "C" {
 
@@ -146,6 +200,7 @@ spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spg
   cudaStream_t s = (cudaStream_t)stream;
   spgemm_plan_s* p = new (std::nothrow) spgemm_plan_s();
   if (!p) return SPGEMM_ERR_ALLOC;
+  p->pinned = pinned_take();
   p->A = to_dev(*A);
   p->B = to_dev(*B);
   p->lim = limits_from(opt);
@@ -163,8 +218,7 @@ spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spg
   int* lists[NUM_CLS] = {nullptr, nullptr, (int*)(p->ws + L.list_w), (int*)(p->ws + L.list_b),
                          (int*)(p->ws + L.list_g)};
   launch_bin(p->A, p->B, p->lim, p->ws + L.cls, lists, p->ctr, s);
-  cudaMemcpyAsync(&p->h, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+  if (read_counters(p, s) != cudaSuccess) {
     delete p;
     return SPGEMM_ERR_CUDA;
   }
@@ -203,8 +257,7 @@ spgemm_status_t spgemm_symbolic(spgemm_plan_t p, int32_t* C_row_ptr, int64_t* nn
     launch_dense_symbolic(p->A, p->B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs,
                           C_row_ptr, p->ctr, s);
   launch_scan(C_row_ptr, (long long)m + 1, (unsigned long long*)(p->ws + L.scan), p->ctr, &p->ctr->nnzC, s);
-  cudaMemcpyAsync(&p->h, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  if (read_counters(p, s) != cudaSuccess) return SPGEMM_ERR_CUDA;
   const spgemm_status_t st = status_from_bits(p->h.status);
   if (st != SPGEMM_OK) return st;
   p->C_rp = C_row_ptr;
@@ -299,8 +352,7 @@ spgemm_status_t spgemm_compute(spgemm_plan_t p, const double* A_val, const doubl
   cudaStream_t s = (cudaStream_t)stream;
   const spgemm_status_t e = compute_enqueue(p, A_val, B_val, C_row_ptr, C_col, C_val, capacity, s);
   if (e != SPGEMM_OK) return e;
-  cudaMemcpyAsync(&p->h, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  if (read_counters(p, s) != cudaSuccess) return SPGEMM_ERR_CUDA;
   const spgemm_status_t st = status_from_bits(p->h.status);
   if (st != SPGEMM_OK) return st;
   *nnz_c = p->h.nnzC;
@@ -335,8 +387,7 @@ spgemm_status_t spgemm_replay_record(spgemm_plan_t p, const int32_t* C_col, void
   if (p->A.rows > 0)
     launch_replay_record(p->A, p->B, p->ws + p->L.cls, p->C_rp, C_col, map,
                          (unsigned long long*)(p->ws + p->L.scan), p->ctr, s);
-  cudaMemcpyAsync(&p->h, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  if (read_counters(p, s) != cudaSuccess) return SPGEMM_ERR_CUDA;
   const spgemm_status_t st = status_from_bits(p->h.status);
   if (st != SPGEMM_OK) return st;
   p->replay_map = map;
@@ -406,8 +457,7 @@ spgemm_status_t spgemm_backward(spgemm_plan_t p, const double* A_val, const doub
 spgemm_status_t spgemm_status(spgemm_plan_t p, void* stream) {
   if (!p) return SPGEMM_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaMemcpyAsync(&p->h, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  if (read_counters(p, s) != cudaSuccess) return SPGEMM_ERR_CUDA;
   return status_from_bits(p->h.status);
 }
 
