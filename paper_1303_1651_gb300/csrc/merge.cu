@@ -51,8 +51,9 @@ enum MergeMode { MODE_SYM = 0, MODE_NUM = 1, MODE_FUSED = 2 };
 template <int MODE, int N, bool DIRECT = false>
 struct SortSmem {
   // Staging: row t's products are contiguous, at pofs_t + t (one slot of skew per row keeps
-  // lanes that read the same position of their rows on different banks).  DIRECT kernels stage
-  // only the columns: values are read from B in the reduce and C is written from there.
+  // lanes that read the same position of their rows on different banks).  The direct form
+  // stages nothing: it reads the columns from B when it builds the keys and the values in the
+  // reduce, and writes C from the reduce; it keeps only the run tables here.
   static constexpr int SLOTS = 32 * N + 32;
   static constexpr bool V = MODE != MODE_SYM;
   static constexpr bool SV = V && !DIRECT;                          // values staged
@@ -63,7 +64,8 @@ struct SortSmem {
   static constexpr size_t s_bofs = r_run + 8 * MAXR;               // int    [8][32]  (DIRECT) B offset of a run rank
   static constexpr size_t s_cfr = s_bofs + (DIRECT ? 4 * 8 * 32 : 0);  // int [N]  (N = 64) run holding product 32c
   static constexpr size_t bytes = s_cfr + (N == 64 ? 4 * N : 0);   // s_a (double [8][32], a_rj by run rank
-                                                                   // and lane) reuses r_run after the expand
+                                                                   // and lane) reuses r_run: after the expand,
+                                                                   // or from the run table on (direct form)
   static_assert(8 * 8 * 32 <= 8 * MAXR, "a table must fit in the run table");
 };
 
