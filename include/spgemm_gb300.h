@@ -95,8 +95,10 @@ typedef struct {
  * strategy switch of the "Combined" kernel (Section IV-B). */
 typedef struct {
   int32_t merge_max_k;    /* rows with k_r <= this (max 8) may use the merge classes (default 8) */
-  int32_t m1_max_u;       /* class M1 (thread-per-row sort of <= 32 products): u_r <= this (max 32, default 32) */
-  int32_t m2_max_u;       /* class M2 (thread-per-row sort of <= 64 products): u_r <= this (max 64, default 64) */
+  int32_t m1_max_u;       /* class M1 (register sort of <= 32 products, one lane per row):
+                             u_r <= this (max 32, default 32) */
+  int32_t m2_max_u;       /* class M2 (register sort of <= 64 products; with the staged values,
+                             two lanes per row): u_r <= this (max 64, default 64) */
   int32_t warp_max_u;     /* warp-per-row class W (bit vector over the row's column range, or a
                              hash table): u_r <= this (max 1024, default 1024) */
   int32_t block_max_u;    /* block-per-row hash class B: u_r <= this (max 4096, default 4096);
@@ -105,11 +107,12 @@ typedef struct {
                              (default 2) */
   int32_t validate;       /* nonzero: also check row_ptr monotonicity and every column index of A and
                              B before planning (one extra pass over both matrices) */
-  int32_t merge_values;   /* classes M1/M2: 0 automatic (default: values of B read in the reduce for
-                             32-product tiles, staged in shared memory for 64-product tiles), 1 read
-                             from B in the reduce and C written from there (less shared memory, more
-                             warps; best when neighbouring rows of A reach neighbouring rows of B),
-                             2 staged with the columns and C written by a coalesced pass */
+  int32_t merge_values;   /* classes M1/M2: 0 automatic (default: the direct form for 32-product
+                             tiles, the staged form for 64-product tiles), 1 direct: columns and
+                             values read from B, C written from the reduce (little shared memory,
+                             more warps; best when neighbouring rows of A reach neighbouring rows of
+                             B), 2 staged: columns and values copied into shared memory with the
+                             tile, C written by a coalesced pass */
   int32_t reserved[8];
 } spgemm_options_t;
 

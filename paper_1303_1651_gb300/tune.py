@@ -2,7 +2,7 @@
 
 The per-row choice between strategies is the paper's "Combined" kernel idea (Section IV-B: a
 cheap per-row decision, tuned by measurement).  Here the choices are the limits of the classes:
-the thread-per-row sort classes M1/M2 (up to 32 / 64 products, at most merge_max_k entries of A),
+the register-sort classes M1/M2 (up to 32 / 64 products, at most merge_max_k entries of A),
 the warp and block hash tables, and the dense fallback.  A merge row with more than 32 products
 switches the whole matrix to the 64-product sort tiles, so capping M2 at 32 (sending such rows to
 the warp hash) is one of the candidates.
@@ -22,8 +22,8 @@ from . import binding
 
 CANDIDATES = [
     {},                                           # defaults: M1 <= 32, M2 <= 64, W <= 1024, B <= 4096
-    {"merge_values": 1},                          # merge classes read B's values in the reduce
-    {"merge_values": 2},                          # merge classes stage B's values
+    {"merge_values": 1},                          # sort classes: direct form (read from B)
+    {"merge_values": 2},                          # sort classes: staged form
     {"m2_max_u": 32, "merge_values": 1},
     {"m2_max_u": 32},                             # 33..64-product rows to the warp hash (32-product tiles)
     {"m1_max_u": 16, "m2_max_u": 32},
