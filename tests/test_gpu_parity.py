@@ -251,3 +251,29 @@ def test_merge_value_modes(mode, fused):
     A = synth.duplicate_entries(synth.random_k(900, 5, 95), 96)
     Bs = synth.shuffle_rows(synth.random_k(900, 6, 97), 98)
     compare(gpu_product(A, Bs, opts(merge_values=mode), fused=fused), oracle.spgemm(A, Bs))
+
+
+def test_more_live_plans_than_pinned_slots():
+    """300 live plans: the first 256 read their counters back through the library's pinned slots,
+    the rest through their own copy; both give the oracle's product."""
+    from paper_1303_1651_gb300 import binding
+    A, B = synth.random_k(200, 3, 97), synth.random_k(200, 3, 98)
+    dA, dB = binding.DeviceCSR.from_host(A), binding.DeviceCSR.from_host(B)
+    R = oracle.spgemm(A, B)
+    prods = []
+    try:
+        for _ in range(300):
+            prods.append(binding.Product(dA, dB))
+        for prod in (prods[0], prods[255], prods[256], prods[299]):
+            out = prod.numeric().to_host()
+            binding.spgemm_status(prod.plan)
+            compare(out, R, single=True)
+    finally:
+        for prod in prods:
+            prod.close()
+    # slots come back with the plans
+    prod = binding.Product(dA, dB)
+    try:
+        compare(prod.numeric().to_host(), R, single=True)
+    finally:
+        prod.close()
