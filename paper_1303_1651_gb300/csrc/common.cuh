@@ -13,9 +13,9 @@ constexpr int KEY_NONE = INT_MAX;       // merge sentinel / empty hash key (vali
 // Row classes chosen by the binning pass (Section IV-B "Combined": a cheap per-row
 // choice of the storing strategy, here of the accumulator).
 enum RowClass : uint8_t {
-  CLS_M1 = 0,   // <= 8 A entries, <= 32 products: thread-per-row merge, 1024-product warp tiles
-  CLS_M2 = 1,   // <= 8 A entries, <= 64 products: thread-per-row merge, 2048-product warp tiles
-  CLS_W = 2,    // warp-per-row shared-memory hash
+  CLS_M1 = 0,   // <= 8 A entries, <= 32 products: register sort, one lane per row, 32-row tiles
+  CLS_M2 = 1,   // <= 8 A entries, <= 64 products: register sort, two lanes per row, 16-row tiles
+  CLS_W = 2,    // warp per row: bit vector, register sort or hash table in shared memory
   CLS_B = 3,    // block-per-row shared-memory hash
   CLS_G = 4,    // dense accumulator in global memory over [min, max] (MinMax)
   NUM_CLS = 5

@@ -1,11 +1,14 @@
 // a2 symbolic and a4 numeric for rows too long for the merge classes.
 //
-// Classes W (a warp per row, 1024-slot table) and B (a 512-thread block per
-// row, 8192-slot table) replace the dense temporary vector of the row-major
+// Class W (a warp per row, up to 1024 products) stages the row's products in
+// shared memory and orders them per row by the cheapest of three ways: a bit
+// vector over the row's column range, a register sort across the warp, or a
+// hash table (details at k_warp_row).  Class B (a 512-thread block per row,
+// 8192-slot table) replaces the dense temporary vector of the row-major
 // algorithm (Section IV-A) with an open-addressing hash table in shared memory
-// (linear probing, bounded to the table size).  The numeric pass then orders
-// the touched columns -- the "Sort" store of Section IV-B -- with a bitonic
-// sort of the compacted table, and appends the row to C.
+// (linear probing, bounded to the table size); its numeric pass orders the
+// touched columns -- the "Sort" store of Section IV-B -- with a bitonic sort of
+// the compacted table, and appends the row to C.
 //
 // Class G (rows beyond the block table) uses the dense temporary vector itself,
 // one per CTA in global memory, scanned over [min, max] of the touched columns
