@@ -341,22 +341,40 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
       int tot;
       const int off = warp_excl_scan(len, &tot);
       if (u + tot > U) { over = true; break; }   // the launch picks U >= every W row: unreachable
-      for (int cb = 0; cb < tot; cb += 32) {
-        const int q = cb + lane;
-        int t = 0;   // last run whose offset is <= q (empty runs share the next run's offset)
+      // WB chunks of 32 products at a time: their runs first, then all their loads in flight
+      constexpr int WB = 4;
+      for (int cb = 0; cb < tot; cb += 32 * WB) {
+        int sp[WB];
+        double at[WB];
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int cnd = t + step;
-          if (__shfl_sync(FULL, off, cnd) <= q) t = cnd;
+        for (int v = 0; v < WB; ++v) {
+          const int q = cb + 32 * v + lane;
+          int t = 0;   // last run whose offset is <= q (empty runs share the next run's offset)
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int cnd = t + step;
+            if (__shfl_sync(FULL, off, cnd) <= q) t = cnd;
+          }
+          sp[v] = __shfl_sync(FULL, bs, t) + (q - __shfl_sync(FULL, off, t));
+          at[v] = NUM ? __shfl_sync(FULL, a, t) : 0.0;
         }
-        const int sp = __shfl_sync(FULL, bs, t) + (q - __shfl_sync(FULL, off, t));
-        const double at = NUM ? __shfl_sync(FULL, a, t) : 0.0;
-        if (q < tot) {
-          const int x = __ldg(B.col + sp);
-          s_col[u + q] = x;
-          if (NUM) s_val[u + q] = __dmul_rn(at, __ldg(B.val + sp));
-          mn = min(mn, x);
-          mx = max(mx, x);
+        int x[WB];
+        double b[WB];
+#pragma unroll
+        for (int v = 0; v < WB; ++v) {
+          const int q = cb + 32 * v + lane;
+          x[v] = q < tot ? __ldg(B.col + sp[v]) : 0;
+          b[v] = (NUM && q < tot) ? __ldg(B.val + sp[v]) : 0.0;
+        }
+#pragma unroll
+        for (int v = 0; v < WB; ++v) {
+          const int q = cb + 32 * v + lane;
+          if (q < tot) {
+            s_col[u + q] = x[v];
+            if (NUM) s_val[u + q] = __dmul_rn(at[v], b[v]);
+            mn = min(mn, x[v]);
+            mx = max(mx, x[v]);
+          }
         }
       }
       u += tot;
