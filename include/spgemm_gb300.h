@@ -150,7 +150,8 @@ spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spg
  *                (C_row_ptr[0] = 0, C_row_ptr[rows] = nnz(C)).
  *   nnz_c     -- host, receives nnz(C) (size C_col/C_val with it).
  * Enqueues on stream and synchronises it.  Errors: STATE, OVERFLOW (nnz(C) > INT32_MAX),
- * TABLE_FULL, TIMEOUT, CUDA.  May be called again (re-runs the symbolic pass). */
+ * TABLE_FULL, TIMEOUT, CUDA; after an error the plan holds no structure and spgemm_numeric
+ * returns STATE.  May be called again (re-runs the symbolic pass). */
 spgemm_status_t spgemm_symbolic(spgemm_plan_t plan, int32_t* C_row_ptr, int64_t* nnz_c, void* stream);
 
 /* a4: compute C's column indices and values.
@@ -173,8 +174,10 @@ spgemm_status_t spgemm_numeric(spgemm_plan_t plan, const double* A_val, const do
  *   C_col, C_val -- device, `capacity` entries each; capacity >= F always suffices.
  *   nnz_c        -- host, receives nnz(C).
  * Enqueues on stream and synchronises it.  Errors: STATE, INVALID, OVERFLOW (nnz(C) > capacity or
- * > INT32_MAX; C's contents are then incomplete), TABLE_FULL, TIMEOUT, CUDA.  After it, the plan is
- * in the same state as after spgemm_symbolic: spgemm_numeric can recompute values in place. */
+ * > INT32_MAX; C's contents are then incomplete, but nothing is written past `capacity` entries
+ * and C_row_ptr's entries are clamped to min(capacity, INT32_MAX)), TABLE_FULL, TIMEOUT, CUDA.  After it
+ * succeeds, the plan is in the same state as after spgemm_symbolic: spgemm_numeric can recompute
+ * values in place; after an error spgemm_numeric returns STATE. */
 spgemm_status_t spgemm_compute(spgemm_plan_t plan, const double* A_val, const double* B_val, int32_t* C_row_ptr,
                                int32_t* C_col, double* C_val, int64_t capacity, int64_t* nnz_c, void* stream);
 
@@ -281,7 +284,7 @@ spgemm_status_t spgemm_free(spgemm_plan_t plan);
  *
  * Errors: INVALID (row_ptr NULL, rows < 0); SCRATCH_LIMIT (rows > SPGEMM_NOALLOC_MAX_ROWS:
  * rejected before any CUDA call, row_ptr untouched); OVERFLOW (a prefix sum exceeds INT32_MAX,
- * row_ptr then holds truncated values); TIMEOUT; CUDA.
+ * entries past it are stored as INT32_MAX); TIMEOUT; CUDA.
  *
  * Set-up: the first call on a device looks up the device address of the scratch array with that
  * device current, and later calls on the device reuse it.  Make that first call before any

@@ -257,6 +257,8 @@ spgemm_status_t spgemm_symbolic(spgemm_plan_t p, int32_t* C_row_ptr, int64_t* nn
     launch_dense_symbolic(p->A, p->B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs,
                           C_row_ptr, p->ctr, s);
   launch_scan(C_row_ptr, (long long)m + 1, (unsigned long long*)(p->ws + L.scan), p->ctr, &p->ctr->nnzC, s);
+  // until a structure pass succeeds, no numeric pass may use a row pointer
+  p->state = 1;
   if (read_counters(p, s) != cudaSuccess) return SPGEMM_ERR_CUDA;
   const spgemm_status_t st = status_from_bits(p->h.status);
   if (st != SPGEMM_OK) return st;
@@ -352,9 +354,9 @@ spgemm_status_t spgemm_compute(spgemm_plan_t p, const double* A_val, const doubl
   cudaStream_t s = (cudaStream_t)stream;
   const spgemm_status_t e = compute_enqueue(p, A_val, B_val, C_row_ptr, C_col, C_val, capacity, s);
   if (e != SPGEMM_OK) return e;
-  if (read_counters(p, s) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  if (read_counters(p, s) != cudaSuccess) { p->state = 1; return SPGEMM_ERR_CUDA; }
   const spgemm_status_t st = status_from_bits(p->h.status);
-  if (st != SPGEMM_OK) return st;
+  if (st != SPGEMM_OK) { p->state = 1; return st; }
   *nnz_c = p->h.nnzC;
   return SPGEMM_OK;
 }

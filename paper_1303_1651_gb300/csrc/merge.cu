@@ -105,6 +105,15 @@ __device__ __forceinline__ void tile_publish(unsigned long long* ts, int tile, l
   if ((threadIdx.x & 31) == 0) atomicExch(&ts[tile], ((unsigned long long)total << 2) | (tile == 0 ? 2ull : 1ull));
 }
 
+// Row pointer entry of a row the fused pass places at pos.  Entries past the capacity of C (or
+// past INT_MAX; rp_cap is the smaller of the two) are stored clamped to it: the hash and dense
+// kernels write row r into [rp[r], rp[r+1]) afterwards, so a product that does not fit leaves
+// them inside C_col / C_val (their rows past the end come out empty) while the status reports
+// the overflow.
+__device__ __forceinline__ int placed_rp(long long pos, int rp_cap) {
+  return (int)min(pos, (long long)rp_cap);
+}
+
 __device__ long long tile_lookback(unsigned long long* ts, int tile, long long total, Counters* ctr) {
   const int lane = threadIdx.x & 31;
   if (tile == 0) return 0;
@@ -146,6 +155,7 @@ struct MergeArgs {
   long long capacity;            // FUSED: entries available in C_col / C_val
   unsigned long long* tile_state;
   Counters* ctr;
+  int rp_cap;                    // FUSED: min(capacity, INT_MAX), the largest row pointer entry stored
 };
 
 template <int MODE, int N, int WARPS, bool DIRECT>
@@ -315,10 +325,10 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
       const long long off = tile_lookback(g.tile_state, tile, TA, g.ctr);
       gstart = off + oa;
       if (inrange) {
-        if (gstart + mycount > INT_MAX) atomicOr(&g.ctr->status, ST_OVERFLOW);
-        g.rp[r] = (int)gstart;
+        if (gstart + mycount > g.rp_cap) atomicOr(&g.ctr->status, ST_OVERFLOW);
+        g.rp[r] = placed_rp(gstart, g.rp_cap);
         if (r == A.rows - 1) {
-          g.rp[r + 1] = (int)(gstart + mycount);
+          g.rp[r + 1] = placed_rp(gstart + mycount, g.rp_cap);
           g.ctr->nnzC = gstart + mycount;
         }
       }
@@ -417,10 +427,10 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
     const long long off = tile_lookback(g.tile_state, tile, TA, g.ctr);
     gstart = off + oa;
     if (inrange) {
-      if (gstart + mycount > INT_MAX) atomicOr(&g.ctr->status, ST_OVERFLOW);
-      g.rp[r] = (int)gstart;
+      if (gstart + mycount > g.rp_cap) atomicOr(&g.ctr->status, ST_OVERFLOW);
+      g.rp[r] = placed_rp(gstart, g.rp_cap);
       if (r == A.rows - 1) {
-        g.rp[r + 1] = (int)(gstart + mycount);
+        g.rp[r + 1] = placed_rp(gstart + mycount, g.rp_cap);
         g.ctr->nnzC = gstart + mycount;
       }
     }
@@ -759,10 +769,10 @@ __device__ __forceinline__ void merge_tile_pair(const MergeArgs& g, int tile, un
     gstart = off + oa_row;
     if (inrange && h == 0) {
       const int rowcount = mine ? cnt : other;
-      if (gstart + rowcount > INT_MAX) atomicOr(&g.ctr->status, ST_OVERFLOW);
-      g.rp[r] = (int)gstart;
+      if (gstart + rowcount > g.rp_cap) atomicOr(&g.ctr->status, ST_OVERFLOW);
+      g.rp[r] = placed_rp(gstart, g.rp_cap);
       if (r == A.rows - 1) {
-        g.rp[r + 1] = (int)(gstart + rowcount);
+        g.rp[r + 1] = placed_rp(gstart + rowcount, g.rp_cap);
         g.ctr->nnzC = gstart + rowcount;
       }
     }
@@ -919,7 +929,8 @@ void launch_merge_numeric(int wide, int values_mode, const DevCsr& A, const DevC
 void launch_merge_fused(int wide, int values_mode, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* rp,
                         int* C_col, double* C_val, long long capacity, unsigned long long* tile_state, Counters* ctr,
                         cudaStream_t s) {
-  MergeArgs g{A, B, rowcls, rp, C_col, C_val, capacity, tile_state, ctr};
+  MergeArgs g{A, B, rowcls, rp, C_col, C_val, capacity, tile_state, ctr,
+              (int)std::min(capacity, (long long)INT_MAX)};
   const bool direct = values_mode == 1 || (values_mode == 0 && !wide);
   if (direct) {
     if (!wide) launch_merge<MODE_FUSED, 32, 1, true>(g, s);

@@ -265,7 +265,7 @@ k_scan(int* __restrict__ rp, long long n, unsigned long long* __restrict__ ts, C
     if (idx < n) {
       const long long e = off + v[i];
       if (e > INT_MAX) ovf = true;
-      rp[idx] = (int)e;
+      rp[idx] = (int)(e > INT_MAX ? (long long)INT_MAX : e);   // clamped when it does not fit
       if (idx == n - 1 && total_out) *total_out = e;
     }
   }

@@ -196,6 +196,40 @@ def test_fused_capacity_too_small_reported():
         binding.spgemm_free(plan)
 
 
+@pytest.mark.parametrize("frac", [0.0, 0.3, 0.7, 0.999])
+def test_fused_capacity_too_small_all_classes(frac):
+    """A capacity below nnz(C) on a product with rows of every class.  The hash and dense kernels
+    write their rows after the fused pass has placed every row, so the row pointer they read must
+    stay inside the capacity: OVERFLOW, C_row_ptr within [0, capacity], nothing written past the
+    capacity, and a numeric pass on the failed structure refused."""
+    import torch
+    from paper_1303_1651_gb300 import binding
+    A = synth.power_law(3000, 3000, 3, alpha=1.5, max_len=3000)
+    B = synth.power_law(3000, 4000, 4, alpha=1.5, max_len=400)
+    nnz = int(oracle.spgemm(A, B)["row_ptr"][-1])
+    dA, dB = binding.DeviceCSR.from_host(A), binding.DeviceCSR.from_host(B)
+    ws = torch.empty(binding.spgemm_workspace_size(dA, dB), dtype=torch.uint8, device="cuda")
+    plan = binding.spgemm_plan(dA, dB, ws)
+    try:
+        cls = binding.spgemm_plan_info(plan)["rows_per_class"]
+        assert all(cls[c] > 0 for c in ("M1", "M2", "W", "B", "G")), cls
+        cap = int(frac * nnz)
+        C_rp = torch.empty(A.rows + 1, dtype=torch.int32, device="cuda")
+        C_col = torch.full((cap + 4096,), -7, dtype=torch.int32, device="cuda")
+        C_val = torch.full((cap + 4096,), 5.0, dtype=torch.float64, device="cuda")
+        with pytest.raises(binding.SpgemmError) as e:
+            binding.spgemm_compute(plan, dA.val, dB.val, C_rp, C_col[:cap], C_val[:cap])
+        assert e.value.name == "SPGEMM_ERR_OVERFLOW"
+        assert bool((C_col[cap:] == -7).all()) and bool((C_val[cap:] == 5.0).all())
+        rp = C_rp.cpu().numpy()
+        assert rp.min() >= 0 and rp.max() <= cap and (np.diff(rp) >= 0).all()
+        with pytest.raises(binding.SpgemmError) as e:
+            binding.spgemm_numeric(plan, dA.val, dB.val, C_col, C_val)
+        assert e.value.name == "SPGEMM_ERR_STATE"
+    finally:
+        binding.spgemm_free(plan)
+
+
 def test_fused_then_numeric_with_new_values():
     import torch
     from paper_1303_1651_gb300 import binding

@@ -68,6 +68,8 @@ def test_empty_and_overflow():
     big = torch.tensor([1 << 30, 1 << 30, 1 << 30, 0], dtype=torch.int32, device="cuda")
     st, total = _noalloc(big, 3)
     assert st == ST_OVERFLOW and total == 3 << 30
+    # the prefix sums that do not fit are stored as INT32_MAX
+    assert big.tolist() == [0, 1 << 30, (1 << 31) - 1, (1 << 31) - 1]
 
 
 def test_size_limit():
