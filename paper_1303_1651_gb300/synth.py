@@ -160,6 +160,27 @@ def sweep_sizes() -> list[int]:
     return [int(round(10 ** (3 + i / 3))) for i in range(13)]
 
 
+SWEEP_KINDS = ("lap", "rand4", "rand8", "rand16")
+
+
+def sweep_points() -> list[tuple[int, str]]:
+    """Every (N, kind) of the size sweep, in increasing N."""
+    return [(N, kind) for N in sweep_sizes() for kind in SWEEP_KINDS]
+
+
+def sweep_problem(N: int, kind: str) -> tuple[CSR, CSR]:
+    """One point of the size sweep.  'lap': C = A*A with A the 5-point Laplacian on a
+    round(sqrt(N))^2 grid (B is A).  'rand<k>': A and B are N x N with k distinct uniform columns
+    per row, seeds SEED_A + N and SEED_B + N."""
+    if kind == "lap":
+        A = laplacian5(max(2, int(round(math.sqrt(N)))))
+        return A, A
+    if not kind.startswith("rand"):
+        raise ValueError(f"unknown sweep kind {kind!r}")
+    k = int(kind[4:])
+    return random_k(N, k, SEED_A + N), random_k(N, k, SEED_B + N)
+
+
 def batch_problems(count: int = 512, seed: int = SEED_BATCH, nmin: int = 256, nmax: int = 65536):
     """Independent (A, B) pairs of uneven sizes: first half Laplacian^2 (B is A), second half random*random."""
     rng = _rng(seed)
