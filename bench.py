@@ -44,15 +44,25 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "medium"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "medium", "batched16"],
                     help="plain: the benchmark workload; medium: Laplacian 1024^2 + random 500K x 8 "
-                         "(inputs above L2, a few hundred MB; for profiler captures)")
+                         "(inputs above L2, a few hundred MB; for profiler captures); batched16: the first "
+                         "16 random x random problems of the batched workload as one block-diagonal product "
+                         "(for captures of the warp-per-row class)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward measurements")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time the size sweep instead (13 log-spaced N from 1e3 to 1e7 for the Laplacian^2 and "
+                         "random*random at 4, 8 and 16 per row; one JSON line with a row per point)")
     ap.add_argument("--verbose", action="store_true")
     return ap.parse_args()
 
 
 def make_workload(kind: str = "plain"):
+    if kind == "batched16":
+        from paper_1303_1651_gb300 import batched
+        probs = synth.batch_problems(count=512, seed=synth.SEED_BATCH)[256:272]
+        A, B, _ = batched.concat(probs)
+        return [("batched16_random", A, B)]
     if kind == "medium":
         L = synth.laplacian5(1024)
         R1 = synth.random_k(500_000, 8, synth.SEED_A)
@@ -134,6 +144,16 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    def sm_median(self, start: int = 0):
+        """Median SM clock of the samples from index start on (None if there are none)."""
+        v = []
+        for ln in self.lines[start:]:
+            try:
+                v.append(float(ln.split(",")[0]))
+            except ValueError:
+                continue
+        return float(np.median(v)) if v else None
+
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -172,6 +192,19 @@ def oracle_rate(work, frac: float, reps: int = 1):
         for _, A, B in work:
             As = row_sample(A, frac)
             F += oracle.spgemm(As, B)["F"]
+    dt = time.perf_counter() - t0
+    return 2 * F / dt / 1e9, dt, F
+
+
+def combined_rate(work, threads: int, frac: float = 1.0):
+    """The paper's Combined CPU kernel (Section IV-B) over the workload, or over the first frac of
+    the rows of A in each product."""
+    import baseline
+    F = 0
+    t0 = time.perf_counter()
+    for _, A, B in work:
+        As = A if frac >= 1.0 else row_sample(A, frac)
+        F += baseline.combined(As, B, threads)["F"]
     dt = time.perf_counter() - t0
     return 2 * F / dt / 1e9, dt, F
 
@@ -360,8 +393,11 @@ def run_ours(args, rank, world, local_rank):
         num_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(p["ev0"], p["ev1"])]))
         cls = p["info"]["rows_per_class"]
         wide = p["info"]["max_row_products"] > 32 and cls["M2"] > 0
-        # default options: 32-product tiles use the direct form, 64-product rows the two-lanes-per-row form
+        # default options: 32-product tiles use the direct form, 64-product rows the two-lanes-per-row form;
+        # longer rows add the warp-, block- and dense-class kernels to the same call
         kern = "k_merge_pair<fused>" if wide else "k_merge<fused,32>"
+        if any(cls[c] > 0 for c in ("W", "B", "G")):
+            kern = "spgemm_compute (" + kern + " + " + ", ".join(c for c in ("W", "B", "G") if cls[c] > 0) + " class kernels)"
         d = {"F": p["info"]["products"], "nnz_c": p["nnz"], "bytes_min": bmin, "compute_ms": num_ms,
              "compute_kernel": kern, "rows_per_class": cls,
              "compute_gbs": bmin / (num_ms * 1e-3) / 1e9,
@@ -385,11 +421,23 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the C ABI from pinned host buffers
     e2e = run_e2e(args, prods, dev, stream, binding, torch, world, dist)
 
-    cpu = None
+    cpu = cpu_combined = None
     if rank == 0 and world == 1:
         rate, dt, F = oracle_rate(work, 1.0 / 16)
         cpu = {"value": rate, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                "sample": f"first 1/16 of the rows of A in each product, full B ({dt:.1f} s, {F} products)"}
+        # the paper's own optimised CPU kernel, on every host thread and on one
+        import baseline
+        threads = baseline.max_threads()
+        combined_rate(work, threads, 1.0 / 64)
+        rate_all, dt_all, _ = combined_rate(work, threads)
+        rate_one, dt_one, _ = combined_rate(work, 1, 0.25)
+        cpu_combined = {"value": rate_all, "unit": "GFLOP/s", "cores": threads,
+                        "kind": "the paper's Combined kernel (Section IV-B), C++ -O3, OpenMP over row chunks",
+                        "sample": f"the whole workload, one step ({dt_all:.2f} s)",
+                        "single_thread": {"value": rate_one, "cores": 1,
+                                          "sample": f"first 1/4 of the rows of A in each product, full B "
+                                                    f"({dt_one:.2f} s)"}}
 
     extras = {}
     if not args.no_extras and args.workload == "plain":
@@ -402,7 +450,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD if args.workload == "plain" else args.workload, "indices": "int32", "values": "float64",
                        "l2": "inputs (~2.5 GB per step) larger than L2; no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_combined": cpu_combined, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(), "detail": detail,
             "three_call": {"ms_per_step": ms_3call, "value": world * flop_step / (ms_3call * 1e-3) / 1e9,
@@ -595,6 +643,95 @@ def run_backward(args, dev, binding, torch):
             "flops_note": "backward does F multiply-adds for dA and F for dB: 4F flops"}
 
 
+def run_sweep(args):
+    """The size sweep on one GPU: per point, plan + single-pass compute (the timed step of the main
+    workload), the L2 flushed before every timed step, times from CUDA events per step."""
+    import torch
+    from paper_1303_1651_gb300 import binding, build
+    build.build()
+    binding.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    bw, bw_kind = hbm_peak()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)    # larger than L2
+    K, W = args.steps, max(args.warmup, 3)
+    points = []
+    with ClockSampler(0) as clk:
+        for N, kind in synth.sweep_points():
+            A, B = synth.sweep_problem(N, kind)
+            dA = binding.DeviceCSR.from_host(A, dev)
+            dB = dA if B is A else binding.DeviceCSR.from_host(B, dev)
+            ws = torch.empty(binding.spgemm_workspace_size(dA, dB), dtype=torch.uint8, device=dev)
+            C_rp = torch.empty(A.rows + 1, dtype=torch.int32, device=dev)
+            pt = {"N": N, "kind": kind, "rows": A.rows, "nnz_a": A.nnz}
+            # nnz(C) and the overflow check from the three-call path, untimed
+            plan = binding.spgemm_plan(dA, dB, ws, None, stream)
+            try:
+                pt["F"] = binding.spgemm_plan_info(plan)["products"]
+                pt["nnz_c"] = binding.spgemm_symbolic(plan, C_rp, stream)
+            except binding.SpgemmError as e:
+                pt["error"] = e.name
+            finally:
+                binding.spgemm_free(plan)
+            if "error" in pt:
+                points.append(pt)
+                continue
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2 * K)]
+            for e in ev:
+                for x in e:
+                    x.record(stream)
+
+            def step(kev=None):
+                plan = binding.spgemm_plan(dA, dB, ws, None, stream)
+                try:
+                    F = binding.spgemm_plan_info(plan)["products"]
+                    C_col = torch.empty(max(F, 1), dtype=torch.int32, device=dev)
+                    C_val = torch.empty(max(F, 1), dtype=torch.float64, device=dev)
+                    if kev:
+                        binding.spgemm_plan_set_events(plan, *kev)
+                    return binding.spgemm_compute(plan, dA.val, dB.val, C_rp, C_col, C_val, stream)
+                finally:
+                    binding.spgemm_free(plan)
+
+            for _ in range(W):
+                step()
+            step_ms, kern_ms = [], []
+            i_clk = len(clk.lines)
+            for i in range(K):
+                flush.zero_()
+                e0, e1 = ev[2 * i]
+                e0.record(stream)
+                nnz = step(ev[2 * i + 1])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                step_ms.append(e0.elapsed_time(e1))
+                kern_ms.append(ev[2 * i + 1][0].elapsed_time(ev[2 * i + 1][1]))
+            assert nnz == pt["nnz_c"]
+            bmin = roofline.bytes_min(A, B, nnz)
+            ms, kms = float(np.median(step_ms)), float(np.median(kern_ms))
+            pt.update({"ms": ms, "gflops": 2 * pt["F"] / (ms * 1e-3) / 1e9, "bytes_min": bmin,
+                       "frac": bmin / (ms * 1e-3) / 1e9 / bw, "kernel_ms": kms,
+                       "kernel_gflops": 2 * pt["F"] / (kms * 1e-3) / 1e9,
+                       "kernel_frac": bmin / (kms * 1e-3) / 1e9 / bw,
+                       "steps_ms": [round(x, 4) for x in step_ms], "sm_mhz": clk.sm_median(i_clk)})
+            points.append(pt)
+            if args.verbose:
+                print(json.dumps(pt), file=sys.stderr, flush=True)
+            del dA, dB, ws, C_rp, A, B
+            torch.cuda.empty_cache()
+    line = {"metric": METRIC, "mode": "sweep", "unit": "GFLOP/s", "n_gpus": 1, "steps": K, "warmup": W,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "size sweep: N = round(10^(3+i/3)), i = 0..12; Laplacian^2 on a round(sqrt N)^2 "
+                                   "grid and random*random with 4, 8, 16 distinct columns per row",
+                       "l2": "512 MB buffer written before every timed step",
+                       "step": "plan (binning, F read back) + single-pass compute (nnz(C) read back)",
+                       "kernel": "the compute call's kernels alone (events around them)"},
+            "peak": {"hbm_gbs": bw, "kind": f"{bw_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+            "clocks": clk.summary(), "points": points}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", 0))
@@ -602,6 +739,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args, rank, world, local_rank)
 
