@@ -261,11 +261,16 @@ def test_fused_then_numeric_with_new_values():
 
 
 @PATHS
-@pytest.mark.parametrize("ncols,k", [(2000, 12), (300_000, 12), (300_000, 30), (6_000_000, 10)],
-                         ids=["bitvector", "regsort-128", "regsort-1024", "hash"])
+@pytest.mark.parametrize("ncols,k", [(2000, 12), (300_000, 12), (300_000, 30), (30_000_000, 10), (16_000_000, 12),
+                                     (30_000_000, 12), (6_000_000, 30), (30_000_000, 4)],
+                         ids=["bitvector", "regsort-256", "regsort-1024", "regsort-128-range-2^25",
+                              "regsort-256-range-2^24", "hash-256", "hash-1024", "hash-16-range-2^25"])
 def test_warp_class_orderings(ncols, k, fused):
     # rows of k entries of A times rows of k entries of B: u = k^2 products, warp class W;
-    # the column range of B picks the ordering (bit vector / register sort / hash table)
+    # the column range of B picks the ordering (bit vector / register sort / hash table).  The
+    # register sort's keys hold the column offset above a 7- to 10-bit product index (by the sort
+    # size that holds u), so it takes ranges below 2^25 (u <= 128) down to 2^22 (u <= 1024); past
+    # 2^22 only rows of more than 32 products take it.
     A = synth.random_k(700, k, 81, ncols=400)
     B = synth.random_k(400, k, 82, ncols=ncols)
     C = gpu_product(A, B, fused=fused)
