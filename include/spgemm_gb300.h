@@ -94,13 +94,19 @@ typedef struct {
  * entries of row r of A) and u_r (its multiplications), in the spirit of the per-row
  * strategy switch of the "Combined" kernel (Section IV-B). */
 typedef struct {
-  int32_t merge_max_k;    /* rows with k_r <= this (max 8) may use the merge classes (default 8) */
+  int32_t merge_max_k;    /* rows with k_r <= this (max 8) may use the merge classes (default 8).
+                             The merge classes need B.cols <= 2^23 - 2 (their 32-bit sort keys hold
+                             the column above 8 or 9 bits of run and product index); for wider B
+                             every row goes to the classes below */
   int32_t m1_max_u;       /* class M1 (register sort of <= 32 products, one lane per row):
                              u_r <= this (max 32, default 32) */
   int32_t m2_max_u;       /* class M2 (register sort of <= 64 products; with the staged values,
                              two lanes per row): u_r <= this (max 64, default 64) */
-  int32_t warp_max_u;     /* warp-per-row class W (bit vector over the row's column range, or a
-                             hash table): u_r <= this (max 1024, default 1024) */
+  int32_t warp_max_u;     /* warp-per-row class W (bit vector over the row's column range; a
+                             register sort across the warp when the range fits its 32-bit keys:
+                             below 2^25 for u_r <= 128 down to 2^22 for u_r > 512, and for u_r <= 32
+                             below 2^22 only; else a hash table): u_r <= this (max 1024, default
+                             1024) */
   int32_t block_max_u;    /* block-per-row hash class B: u_r <= this (max 4096, default 4096);
                              longer rows use a dense accumulator in global memory (class G) */
   int32_t dense_slabs;    /* CTAs (each owning one dense accumulator of B.cols doubles) for class G
