@@ -100,7 +100,9 @@ def combined(A, B, threads: int | None = None) -> dict:
                                   C_rp, C_col, C_val, S_col, S_val, stats))
     if nnz == -1:
         raise ValueError("a column index of B is out of range")
-    if nnz < 0:
+    if nnz == -2:
         raise MemoryError("combined_spgemm could not allocate its temporary vectors")
+    if nnz < 0:
+        raise RuntimeError(f"combined_spgemm failed ({nnz})")
     return dict(rows=A.rows, cols=B.cols, row_ptr=C_rp, col_idx=C_col[:nnz], val=C_val[:nnz], nnz=nnz, F=F,
                 rows_minmax=int(stats[0]), rows_sort=int(stats[1]), threads=threads)

@@ -139,19 +139,23 @@ int64_t combined_products(int64_t m, int64_t k, const int32_t* A_rp, const int32
 //   C_rp     -- m + 1 entries; C_col / C_val: F entries each.
 //   S_col / S_val -- F entries each of scratch (used with more than one thread; may alias nothing).
 //   stats    -- receives the rows stored by MinMax and by Sort.
-// Returns nnz(C), or -1 if a column of B is out of range, -2 on allocation failure.
+// Returns nnz(C), or -1 if a column of B is out of range, -2 on allocation failure, -3 if the
+// counts u do not sum to F.
 int64_t combined_spgemm(int64_t m, int64_t k, int64_t n, const int32_t* A_rp, const int32_t* A_col,
                         const double* A_val, const int32_t* B_rp, const int32_t* B_col, const double* B_val,
                         const int64_t* u, int64_t F, int threads, int64_t* C_rp, int32_t* C_col, double* C_val,
                         int32_t* S_col, double* S_val, int64_t* stats) {
-  (void)k;
   stats[0] = stats[1] = 0;
   C_rp[0] = 0;
   if (m == 0) return 0;
   for (int64_t q = 0; q < B_rp[k]; ++q)
     if (B_col[q] < 0 || B_col[q] >= n) return -1;
-  int64_t umax = 0;
-  for (int64_t r = 0; r < m; ++r) umax = std::max(umax, u[r]);
+  int64_t umax = 0, total = 0;
+  for (int64_t r = 0; r < m; ++r) {
+    umax = std::max(umax, u[r]);
+    total += u[r];
+  }
+  if (total != F) return -3;
 #ifndef _OPENMP
   threads = 1;
 #endif
@@ -174,7 +178,6 @@ int64_t combined_spgemm(int64_t m, int64_t k, int64_t n, const int32_t* A_rp, co
     for (int64_t r = c * CHUNK_ROWS; r < std::min(m, (c + 1) * CHUNK_ROWS); ++r) s += u[r];
     ub[(size_t)c + 1] = ub[(size_t)c] + s;
   }
-  (void)F;
   int64_t minmax = 0, sorted = 0;
   bool failed = false;
 #ifdef _OPENMP
