@@ -93,7 +93,7 @@ __global__ void k_validate(DevCsr M, Counters* ctr) {
 namespace {
 
 // Counters are read back to the host after every synchronising call.  Through pinned memory
-// that is one DMA; through pageable memory the driver stages the copy.  A small pinned buffer,
+// that is one DMA; through pageable memory the CUDA driver stages the copy.  A small pinned buffer,
 // allocated once per process on first use, gives each live plan a slot while slots last (plans
 // beyond that read into their own pageable copy).
 constexpr int PINNED_SLOTS = 256;
