@@ -67,7 +67,8 @@ typedef enum {
   SPGEMM_ERR_INVALID = 1,     /* bad argument: NULL pointer, negative size, A.cols != B.rows,
                                  a column index out of range, a decreasing row pointer */
   SPGEMM_ERR_ALLOC = 2,       /* the workspace passed is smaller than spgemm_workspace_size */
-  SPGEMM_ERR_OVERFLOW = 3,    /* nnz(C), or the products of one row, exceed INT32_MAX */
+  SPGEMM_ERR_OVERFLOW = 3,    /* nnz(C) exceeds INT32_MAX (or the capacity given to spgemm_compute),
+                                 or the products of one row exceed INT32_MAX */
   SPGEMM_ERR_TABLE_FULL = 4,  /* a hash table ran out of slots (cannot happen within the class limits) */
   SPGEMM_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed */
   SPGEMM_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
