@@ -74,3 +74,16 @@ def test_cpu_baseline_helpers():
     rate, dt, F = bench.oracle_rate(work, 0.5)
     assert rate > 0 and F == oracle.spgemm(bench.row_sample(A, 0.5), B)["F"] + \
         oracle.spgemm(bench.row_sample(work[1][1], 0.5), work[1][1])["F"]
+
+
+def test_combined_baseline_entry(monkeypatch):
+    bench = load_bench()
+    work = [("r", synth.random_k(4000, 8, 7), synth.random_k(4000, 8, 8))]
+    line = bench.combined_baseline(work)
+    assert line["value"] > 0 and line["cores"] >= 1 and line["single_thread"]["cores"] == 1
+    import baseline
+
+    def broken(*a, **k):
+        raise OSError("no C++ compiler")
+    monkeypatch.setattr(baseline, "combined", broken)
+    assert bench.combined_baseline(work) == {"unavailable": "OSError: no C++ compiler"}
