@@ -7,8 +7,6 @@
 // is sized for SPGEMM_NOALLOC_MAX_ROWS rows; every device that runs this code holds it (about
 // 256 KiB) until the process exits.  Nothing here calls cudaMalloc, cudaFree or any routine that
 // allocates device memory.
-#include <mutex>
-
 #include "internal.h"
 #include "spgemm_gb300.h"
 
@@ -26,25 +24,16 @@ constexpr size_t SCRATCH_WORDS = NOALLOC_HEADER_BYTES / 8 + (size_t)((NOALLOC_MA
 static __device__ __align__(256) unsigned long long g_scan_scratch[SCRATCH_WORDS];
 static_assert(sizeof(g_scan_scratch) == SPGEMM_NOALLOC_SCRATCH_BYTES, "stated scratch size out of date");
 
-// Device address of g_scan_scratch, looked up once per device with that device current.
-constexpr int MAX_DEVICES = 64;
-std::mutex g_setup_mu;
-void* g_scratch_ptr[MAX_DEVICES] = {};
-
+// Device address of g_scan_scratch in the current context.  It is looked up on every call, with
+// the caller's device current: the address belongs to the context that loaded this module, and a
+// context made later on the same device (after a device reset, or a driver context of the
+// caller's own) loads the module at another address.  The lookup allocates nothing.
 cudaError_t scratch_for_current_device(void** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scan_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scan_scratch);
-    if (e != cudaSuccess) return e;
-    if (!p) return cudaErrorInvalidSymbol;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  if (!p) return cudaErrorInvalidSymbol;
+  *out = p;
   return cudaSuccess;
 }
 

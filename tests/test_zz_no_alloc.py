@@ -38,11 +38,12 @@ def _counts_buffer(rp):
     return buf
 
 
-def _noalloc(buf, rows):
+def _noalloc(buf, rows, stream=None):
     lib = binding.load()
     total = ctypes.c_int64(-1)
+    s = stream if stream is not None else torch.cuda.current_stream()
     st = lib.spgemm_scan_counts_noalloc(ctypes.c_void_p(buf.data_ptr()), ctypes.c_int64(rows), ctypes.byref(total),
-                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+                                        ctypes.c_void_p(s.cuda_stream))
     return st, total.value
 
 
@@ -86,3 +87,23 @@ def test_size_limit():
     assert int(buf.min()) == 5 and int(buf.max()) == 5
     with pytest.raises(binding.SpgemmError, match="SCRATCH_LIMIT"):
         binding.spgemm_scan_counts_noalloc(buf, MAX_ROWS + 1)
+
+
+def test_ordered_on_a_caller_stream():
+    # The counts are written by kernels queued on a side stream (behind a spin of about a
+    # millisecond), and the entry point is called on that stream with no host synchronisation in
+    # between: its clearing of the scratch, its scan and its read-back must run after them.
+    A, B = synth.random_k(50_001, 6, seed=21), synth.random_k(50_001, 6, seed=22)
+    rp, nnz = _symbolic_row_ptr(A, B)
+    counts = rp[1:] - rp[:-1]
+    buf = torch.full_like(rp, -1)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(2_000_000)
+        torch.add(counts, 0, out=buf[:-1])
+        st, total = _noalloc(buf, rp.numel() - 1, stream=side)
+    assert st == 0, binding.error_string(st)
+    assert total == nnz
+    torch.cuda.synchronize()
+    assert torch.equal(buf, rp)
