@@ -50,7 +50,10 @@
  * Errors: every function returns an spgemm_status_t.  Device-side errors
  * (table overflow, a changed pattern, a bounded wait that gave up) are sticky
  * in the plan and are reported by the next synchronising call, or by
- * spgemm_status.  No kernel traps or waits without a bound.
+ * spgemm_status.  Each structure pass (spgemm_symbolic, spgemm_compute,
+ * spgemm_compute_async) starts from a clear status, so a product can be retried
+ * on the same plan, e.g. with a larger C after SPGEMM_ERR_OVERFLOW.  No kernel
+ * traps or waits without a bound.
  */
 #ifndef SPGEMM_GB300_H
 #define SPGEMM_GB300_H
@@ -96,9 +99,9 @@ typedef struct {
  * strategy switch of the "Combined" kernel (Section IV-B). */
 typedef struct {
   int32_t merge_max_k;    /* rows with k_r <= this (max 8) may use the merge classes (default 8).
-                             The merge classes need B.cols <= 2^23 - 2 (their 32-bit sort keys hold
-                             the column above 8 or 9 bits of run and product index); for wider B
-                             every row goes to the classes below */
+                             The merge classes need B.cols <= 2^26 - 2 (their 32-bit sort keys hold
+                             the column above 5 or 6 bits of product index); for wider B every row
+                             goes to the classes below */
   int32_t m1_max_u;       /* class M1 (register sort of <= 32 products, one lane per row):
                              u_r <= this (max 32, default 32) */
   int32_t m2_max_u;       /* class M2 (register sort of <= 64 products; with the staged values,
@@ -110,8 +113,9 @@ typedef struct {
                              1024) */
   int32_t block_max_u;    /* block-per-row hash class B: u_r <= this (max 4096, default 4096);
                              longer rows use a dense accumulator in global memory (class G) */
-  int32_t dense_slabs;    /* CTAs (each owning one dense accumulator of B.cols doubles) for class G
-                             (default 2) */
+  int32_t dense_slabs;    /* CTAs (each owning one dense accumulator of B.cols doubles and flags, 12
+                             bytes per column) for class G; default: as many as fit in 128 MB, at
+                             least 2 and at most one per SM of the current device */
   int32_t validate;       /* nonzero: also check row_ptr monotonicity and every column index of A and
                              B before planning (one extra pass over both matrices) */
   int32_t merge_values;   /* classes M1/M2: 0 automatic (default: the direct form for 32-product
@@ -120,7 +124,36 @@ typedef struct {
                              more warps; best when neighbouring rows of A reach neighbouring rows of
                              B), 2 staged: columns and values copied into shared memory with the
                              tile, C written by a coalesced pass */
-  int32_t reserved[8];
+  int32_t a_storage;      /* 0: A is in compressed rows (CSR).  1: A is in compressed columns (CSC): its
+                             descriptor keeps A's own rows and cols, but row_ptr holds cols + 1 column
+                             pointers and col_idx the row index of every entry, and A's values are
+                             passed in that column-major order (Section IV-A, mixed storage orders).
+                             The plan converts the structure once, into the workspace, with the
+                             counting-sort transpose; every call that takes A's values gathers them
+                             into row order first, and spgemm_backward returns dA in column order.
+                             Within a row the converted entries are ordered by column, then by
+                             position in the given arrays */
+  int32_t b_storage;      /* the same for B */
+  int32_t warp_bitvec_ratio;  /* class W: a row is ordered by a bit vector over its column range when
+                             that range holds at most this many columns per product of the row
+                             (1 .. 128, default 128, i.e. 4 bit-vector words per product).  2 is the
+                             switch of the paper's "Combined" kernel (Section IV-B: MinMax when the
+                             range is below twice the row's entries), with the row's products
+                             standing in for its entries, which are not known before the ordering */
+  int32_t warp_order;     /* class W: 0 automatic (the bit vector as above, else the register sort
+                             when its keys fit, else the hash table), 1 the bit vector whenever the
+                             range fits it (at most 4 words per product and 65536 columns), 2 the
+                             register sort whenever its keys fit, 3 always the hash table */
+  int32_t debug_spin_limit;   /* testing: rounds of re-reads after which a look-back of the single-pass
+                             product gives up (0: 2^24).  With a small limit and debug_drop_tile, a
+                             test can make the wait run out (SPGEMM_ERR_TIMEOUT) */
+  int32_t debug_drop_tile;    /* testing: 0 none; t > 0: tile t - 1 of the single-pass product (tiles
+                             of 32 rows, or 16 where some sort-class row has more than 32 products)
+                             publishes neither its entry count nor its prefix, so the look-backs
+                             that reach it give up after debug_spin_limit rounds.  C is then wrong
+                             and spgemm_compute returns SPGEMM_ERR_TIMEOUT; nothing is written
+                             outside the caller's buffers */
+  int32_t reserved[2];
 } spgemm_options_t;
 
 /* Counters of a plan, valid after spgemm_plan (and nnz_c after spgemm_symbolic). */
@@ -275,8 +308,8 @@ spgemm_status_t spgemm_free(spgemm_plan_t plan);
  * would change a footprint they must hold constant.
  *
  * It performs the step that spgemm_symbolic uses to turn the per-row entry counts of C into C's
- * row pointers: an exclusive prefix sum over rows (the contiguous row-by-row storage of C,
- * Section IV-B), by the same single-pass scan kernel.  Instead of a workspace, the scan's scratch
+ * row pointers: an exclusive prefix sum of the per-row counts into row pointers, by the same
+ * single-pass scan kernel.  Instead of a workspace, the scan's scratch
  * (one state word per 2048 rows plus a 256-byte header) lives in a fixed device array of
  * SPGEMM_NOALLOC_SCRATCH_BYTES bytes, which every device that runs this call keeps until the
  * process exits.  That array bounds the size: at most SPGEMM_NOALLOC_MAX_ROWS rows.
@@ -293,9 +326,12 @@ spgemm_status_t spgemm_free(spgemm_plan_t plan);
  * rejected before any CUDA call, row_ptr untouched); OVERFLOW (a prefix sum exceeds INT32_MAX,
  * entries past it are stored as INT32_MAX); TIMEOUT; CUDA.
  *
- * Set-up: the first call on a device looks up the device address of the scratch array with that
- * device current, and later calls on the device reuse it.  Make that first call before any
- * stream capture begins.
+ * Set-up: every call looks up the device address of the scratch array in the current context
+ * (the lookup allocates nothing), so a device reset or another context between calls is safe.
+ *
+ * Capture: the call copies its counters to the host and synchronises `stream`, so it must not be
+ * called while `stream` (or, in the global capture mode, any stream) is being captured into a
+ * CUDA graph.
  *
  * Concurrency: all calls on one device share the one scratch array.  Calls that overlap in time,
  * from several host threads or on several streams, race on it and give wrong results: serialise

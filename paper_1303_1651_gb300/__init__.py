@@ -6,7 +6,8 @@ Matrix-Matrix Multiplication" (arXiv:1303.1651), re-designed as sm_103a CUDA
 kernels behind the C ABI in include/spgemm_gb300.h.
 
 Submodules:
-  binding  -- ctypes binding of the C ABI (loads the CUDA library; no CPU fallback)
+  binding  -- ctypes binding of the C ABI (loads the CUDA library; no CPU fallback), and
+              spgemm(A, B), the product of torch sparse CSR/CSC tensors
   synth    -- seeded synthetic inputs (FD 5-point Laplacian, random k per row, batches)
   roofline -- bytes/flops accounting of the product and the paper's balance model
   build    -- nvcc build of the library
@@ -20,6 +21,8 @@ __version__ = "1.0.0"
 
 def __getattr__(name):
     import importlib
+    if name == "spgemm":
+        return importlib.import_module(".binding", __name__).spgemm
     if name in ("binding", "synth", "build", "roofline", "autograd", "batched", "tune", "ranks"):
         return importlib.import_module(f".{name}", __name__)
     raise AttributeError(name)

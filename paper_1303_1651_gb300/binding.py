@@ -41,7 +41,10 @@ class spgemm_csr_t(ctypes.Structure):
 class spgemm_options_t(ctypes.Structure):
     _fields_ = [("merge_max_k", ctypes.c_int32), ("m1_max_u", ctypes.c_int32), ("m2_max_u", ctypes.c_int32),
                 ("warp_max_u", ctypes.c_int32), ("block_max_u", ctypes.c_int32), ("dense_slabs", ctypes.c_int32),
-                ("validate", ctypes.c_int32), ("merge_values", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("validate", ctypes.c_int32), ("merge_values", ctypes.c_int32), ("a_storage", ctypes.c_int32),
+                ("b_storage", ctypes.c_int32), ("warp_bitvec_ratio", ctypes.c_int32), ("warp_order", ctypes.c_int32),
+                ("debug_spin_limit", ctypes.c_int32), ("debug_drop_tile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class spgemm_info_t(ctypes.Structure):
@@ -143,6 +146,37 @@ class DeviceCSR:
     def to_host(self) -> dict:
         return dict(rows=self.rows, cols=self.cols, row_ptr=self.row_ptr.cpu().numpy(),
                     col_idx=self.col_idx.cpu().numpy(), val=self.val.cpu().numpy(), nnz=self.nnz)
+
+
+@dataclass
+class DeviceCSC:
+    """Matrix in compressed columns in device memory: int32 col_ptr (cols + 1), int32 row_idx, float64
+    val.  Passed to the library with the option a_storage / b_storage = 1 (the descriptor keeps the
+    matrix's own rows and cols; its row_ptr and col_idx fields carry col_ptr and row_idx)."""
+
+    rows: int
+    cols: int
+    col_ptr: torch.Tensor
+    row_idx: torch.Tensor
+    val: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_idx.numel())
+
+    def desc(self, with_values: bool = True) -> spgemm_csr_t:
+        return spgemm_csr_t(self.rows, self.cols, self.nnz, _ptr(self.col_ptr), _ptr(self.row_idx),
+                            _ptr(self.val) if with_values else None)
+
+
+def with_storage(A, B, opt: spgemm_options_t | None = None) -> spgemm_options_t | None:
+    """opt (copied) with a_storage / b_storage set for operands given as DeviceCSC."""
+    a, b = isinstance(A, DeviceCSC), isinstance(B, DeviceCSC)
+    if not (a or b or (opt is not None and (opt.a_storage or opt.b_storage))):
+        return opt
+    o = spgemm_options_t.from_buffer_copy(opt) if opt is not None else spgemm_options_t()
+    o.a_storage, o.b_storage = int(a), int(b)
+    return o
 
 
 def options(**kw) -> spgemm_options_t:
@@ -285,8 +319,9 @@ class Product:
                  workspace: torch.Tensor | None = None):
         if A.cols != B.rows:
             raise ValueError("inner dimensions differ")
+        opt = with_storage(A, B, opt)
         self.A, self.B, self.opt = A, B, opt
-        dev = A.row_ptr.device
+        dev = A.val.device
         need = spgemm_workspace_size(A, B, opt)
         if workspace is None or workspace.numel() < need:
             workspace = torch.empty(need, dtype=torch.uint8, device=dev)
@@ -297,7 +332,7 @@ class Product:
         self.info = spgemm_plan_info(self.plan)
 
     def numeric(self, A_val=None, B_val=None, C_col=None, C_val=None, stream=None) -> DeviceCSR:
-        dev = self.A.row_ptr.device
+        dev = self.A.val.device
         A_val = self.A.val if A_val is None else A_val
         B_val = self.B.val if B_val is None else B_val
         if C_col is None:
@@ -309,14 +344,14 @@ class Product:
 
     def record(self, C: DeviceCSR, stream=None):
         """Record the position map of C's structure (a result of numeric) for replay()."""
-        self.map = torch.empty(spgemm_replay_size(self.plan), dtype=torch.uint8, device=self.A.row_ptr.device)
+        self.map = torch.empty(spgemm_replay_size(self.plan), dtype=torch.uint8, device=self.A.val.device)
         spgemm_replay_record(self.plan, C.col_idx, self.map, stream)
         self.C_col = C.col_idx
 
     def replay(self, A_val, B_val, C_val=None, stream=None) -> DeviceCSR:
         """C's values for new values of A and B, through the recorded map (same bits as numeric)."""
         if C_val is None:
-            C_val = torch.empty(self.nnz, dtype=torch.float64, device=self.A.row_ptr.device)
+            C_val = torch.empty(self.nnz, dtype=torch.float64, device=self.A.val.device)
         spgemm_replay(self.plan, A_val, B_val, self.map, self.C_col, C_val, stream)
         return DeviceCSR(self.A.rows, self.B.cols, self.C_row_ptr, self.C_col, C_val)
 
@@ -348,7 +383,8 @@ def multiply(A: DeviceCSR, B: DeviceCSR, opt: spgemm_options_t | None = None, st
 def multiply_fused(A: DeviceCSR, B: DeviceCSR, opt: spgemm_options_t | None = None, stream=None,
                    workspace: torch.Tensor | None = None, trim: bool = True) -> DeviceCSR:
     """C = A*B through plan and the single-pass spgemm_compute (C sized by the multiplication count)."""
-    dev = A.row_ptr.device
+    opt = with_storage(A, B, opt)
+    dev = A.val.device
     need = spgemm_workspace_size(A, B, opt)
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=dev)
@@ -364,3 +400,45 @@ def multiply_fused(A: DeviceCSR, B: DeviceCSR, opt: spgemm_options_t | None = No
     if trim:
         C_col, C_val = C_col[:nnz], C_val[:nnz]
     return DeviceCSR(A.rows, B.cols, C_rp, C_col, C_val)
+
+
+# ---- torch front door ------------------------------------------------------------------------
+
+def _from_torch(M: torch.Tensor, name: str):
+    """A torch sparse CSR or CSC tensor (CUDA, int32 indices, float64 values) as a DeviceCSR/DeviceCSC."""
+    if not isinstance(M, torch.Tensor) or M.layout not in (torch.sparse_csr, torch.sparse_csc):
+        raise TypeError(f"{name} must be a torch.sparse_csr_tensor or torch.sparse_csc_tensor")
+    if M.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D matrix (batched sparse tensors are not supported)")
+    if not M.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    rows, cols = M.shape
+    if M.layout == torch.sparse_csr:
+        ptr, idx = M.crow_indices(), M.col_indices()
+    else:
+        ptr, idx = M.ccol_indices(), M.row_indices()
+    val = M.values()
+    if ptr.dtype != torch.int32 or idx.dtype != torch.int32:
+        raise TypeError(f"{name} must have int32 indices (build it with crow/col index tensors of dtype int32)")
+    if val.dtype != torch.float64:
+        raise TypeError(f"{name} must have float64 values")
+    ptr, idx, val = ptr.contiguous(), idx.contiguous(), val.contiguous()
+    if M.layout == torch.sparse_csr:
+        return DeviceCSR(rows, cols, ptr, idx, val)
+    return DeviceCSC(rows, cols, ptr, idx, val)
+
+
+def spgemm(A: torch.Tensor, B: torch.Tensor, opt: spgemm_options_t | None = None, stream=None) -> torch.Tensor:
+    """C = A @ B for sparse matrices on a CUDA device; returns a torch.sparse_csr_tensor.
+
+    A and B are torch.sparse_csr_tensor or torch.sparse_csc_tensor (any mix), int32 indices, float64
+    values, any shapes with A.shape[1] == B.shape[0].  An operand in CSC is converted to rows inside
+    the library (Section IV-A's storage-order conversion).  C's rows are sorted by column, with every
+    structural entry kept, and C is computed by spgemm_plan + spgemm_compute (C sized by the
+    multiplication count, then trimmed).  For gradients with respect to the values, use
+    autograd.SpGEMMFunction."""
+    a, b = _from_torch(A, "A"), _from_torch(B, "B")
+    if a.cols != b.rows:
+        raise ValueError(f"inner dimensions differ: A is {a.rows}x{a.cols}, B is {b.rows}x{b.cols}")
+    C = multiply_fused(a, b, opt, stream)
+    return torch.sparse_csr_tensor(C.row_ptr, C.col_idx, C.val, size=(a.rows, b.cols))

@@ -16,11 +16,17 @@ namespace {
 constexpr size_t ALIGN = 256;
 inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
+// Workspace pieces.  conv/cval/cgrad exist for an operand given in compressed columns: its
+// structure converted to rows (row pointers, column indices and, per entry, its position in the
+// given arrays: the transpose's output), its values gathered into that order for each call, and
+// its gradient before it is scattered back (spgemm_backward).
 struct Layout {
   size_t ctr, cls, list_w, list_b, list_g, scan, fused, slabs, total;
+  size_t conv[2], cval[2], cgrad[2];
 };
 
-Layout layout(int m, int ncols, int nslabs) {
+Layout layout(const spgemm_csr_t& A, const spgemm_csr_t& B, int nslabs, const bool csc[2]) {
+  const int m = A.rows;
   Layout L{};
   size_t o = 0;
   L.ctr = o; o += up(sizeof(Counters));
@@ -30,7 +36,15 @@ Layout layout(int m, int ncols, int nslabs) {
   L.list_g = o; o += up(4 * (size_t)std::max(m, 1));
   L.scan = o; o += up(scan_tile_state_bytes((long long)m + 1) + 64);
   L.fused = o; o += up(fused_tile_state_bytes(m) + 64);
-  L.slabs = o; o += (size_t)nslabs * dense_slab_bytes(ncols);
+  L.slabs = o; o += (size_t)nslabs * dense_slab_bytes(B.cols);
+  const spgemm_csr_t* M[2] = {&A, &B};
+  for (int i = 0; i < 2; ++i) {
+    if (!csc[i]) continue;
+    const size_t n = (size_t)std::max(M[i]->nnz, (int64_t)1);
+    L.conv[i] = o; o += up(transpose_bytes(M[i]->rows, M[i]->nnz));
+    L.cval[i] = o; o += up(8 * n);
+    L.cgrad[i] = o; o += up(8 * n);
+  }
   L.total = o;
   return L;
 }
@@ -52,17 +66,46 @@ Limits limits_from(const spgemm_options_t* o) {
   return l;
 }
 
-int slabs_from(const spgemm_options_t* o) { return (o && o->dense_slabs > 0) ? o->dense_slabs : 2; }
+// Dense accumulators of class G, one per CTA: the caller's number, else as many as fit 128 MB
+// (at least 2, at most one per SM).
+WarpOrder wopts_from(const spgemm_options_t* o) {
+  WarpOrder w;
+  if (o && o->warp_bitvec_ratio > 0) w.bitvec_ratio = std::min(o->warp_bitvec_ratio, 128);
+  if (o && o->warp_order >= 0 && o->warp_order <= 3) w.order = o->warp_order;
+  return w;
+}
 
-bool desc_ok(const spgemm_csr_t* M) {
+int slabs_from(const spgemm_options_t* o, int ncols) {
+  if (o && o->dense_slabs > 0) return o->dense_slabs;
+  const size_t fit = ((size_t)128 << 20) / dense_slab_bytes(ncols);
+  return (int)std::max<size_t>(2, std::min<size_t>(fit, (size_t)num_sms()));
+}
+
+bool csc_of(const spgemm_options_t* o, int i) { return o && (i == 0 ? o->a_storage : o->b_storage) == 1; }
+
+bool storage_ok(const spgemm_options_t* o) {
+  return !o || ((o->a_storage == 0 || o->a_storage == 1) && (o->b_storage == 0 || o->b_storage == 1));
+}
+
+// A descriptor in compressed rows, or (csc) in compressed columns: then row_ptr has cols + 1 entries.
+bool desc_ok(const spgemm_csr_t* M, bool csc = false) {
   if (!M || M->rows < 0 || M->cols < 0 || M->nnz < 0 || M->nnz > INT32_MAX) return false;
-  if (!M->row_ptr && M->rows > 0) return false;
+  if (!M->row_ptr && (csc ? M->cols : M->rows) > 0) return false;
   if (!M->col_idx && M->nnz > 0) return false;
   return true;
 }
 
 DevCsr to_dev(const spgemm_csr_t& M) {
   return DevCsr{M.rows, M.cols, (long long)M.nnz, M.row_ptr, M.col_idx, M.val};
+}
+
+// Host-side fault injection for tests of the error paths, read from the environment at each call:
+// SPGEMM_FAULT=alloc makes spgemm_plan report a workspace that is too small; SPGEMM_FAULT=nnz_overflow
+// makes spgemm_symbolic report nnz(C) past INT32_MAX and the single-pass product run with no room
+// for C (its device overflow path).  Nothing is injected on the device.
+bool fault_is(const char* name) {
+  const char* f = std::getenv("SPGEMM_FAULT");
+  return f && std::strcmp(f, name) == 0;
 }
 
 spgemm_status_t status_from_bits(unsigned bits) {
@@ -129,10 +172,17 @@ void pinned_give(Counters* c) {
 }  // namespace
 
 struct spgemm_plan_s {
-  DevCsr A{}, B{};
+  DevCsr A{}, B{};              // in compressed rows (converted in the workspace when given by columns)
+  bool csc[2] = {false, false}; // A, B given in compressed columns
+  const int* perm[2] = {nullptr, nullptr};   // converted entry -> position in the given arrays
+  double* cval[2] = {nullptr, nullptr};      // values gathered into row order
+  double* cgrad[2] = {nullptr, nullptr};     // gradients in row order, before the scatter
+  int spin_limit = 0;           // look-back bound of the single-pass product (0: default)
+  int drop_tile = -1;           // testing: a fused tile that publishes nothing (-1: none)
   Limits lim{};
   int nslabs = 0;
   int values_mode = 0;          // merge classes: 0 automatic, 1 values read from B, 2 staged
+  WarpOrder wopt{};             // ordering of the class-W rows
   Layout L{};
   unsigned char* ws = nullptr;
   Counters* ctr = nullptr;
@@ -160,6 +210,20 @@ cudaError_t read_counters(spgemm_plan_s* p, cudaStream_t s) {
 }
 }  // namespace
 
+namespace {
+// Values of A and B as the kernels read them: the caller's arrays, or for an operand given by
+// columns its values gathered into the converted row order.
+void prepare_values(spgemm_plan_s* p, const double* A_val, const double* B_val, DevCsr& A, DevCsr& B,
+                    cudaStream_t s) {
+  A = p->A;
+  B = p->B;
+  A.val = A_val;
+  B.val = B_val;
+  if (p->csc[0] && A_val) { launch_gather(p->perm[0], A_val, p->cval[0], p->A.nnz, s); A.val = p->cval[0]; }
+  if (p->csc[1] && B_val) { launch_gather(p->perm[1], B_val, p->cval[1], p->B.nnz, s); B.val = p->cval[1]; }
+}
+}  // namespace
+
 extern "C" {
 
 int32_t spgemm_version(void) { return 10000; }
@@ -183,8 +247,10 @@ const char* spgemm_error_string(int code) {
 
 spgemm_status_t spgemm_workspace_size(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
                                       size_t* bytes) {
-  if (!bytes || !desc_ok(A) || !desc_ok(B) || A->cols != B->rows) return SPGEMM_ERR_INVALID;
-  *bytes = layout(A->rows, B->cols, slabs_from(opt)).total;
+  if (!bytes || !storage_ok(opt)) return SPGEMM_ERR_INVALID;
+  const bool csc[2] = {csc_of(opt, 0), csc_of(opt, 1)};
+  if (!desc_ok(A, csc[0]) || !desc_ok(B, csc[1]) || A->cols != B->rows) return SPGEMM_ERR_INVALID;
+  *bytes = layout(*A, *B, slabs_from(opt, B->cols), csc).total;
   return SPGEMM_OK;
 }
 
@@ -192,11 +258,13 @@ spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spg
                             const spgemm_options_t* opt, void* workspace, size_t workspace_bytes, void* stream) {
   if (!out) return SPGEMM_ERR_INVALID;
   *out = nullptr;
-  if (!desc_ok(A) || !desc_ok(B) || A->cols != B->rows) return SPGEMM_ERR_INVALID;
+  if (!storage_ok(opt)) return SPGEMM_ERR_INVALID;
+  const bool csc[2] = {csc_of(opt, 0), csc_of(opt, 1)};
+  if (!desc_ok(A, csc[0]) || !desc_ok(B, csc[1]) || A->cols != B->rows) return SPGEMM_ERR_INVALID;
   if (!workspace || ((uintptr_t)workspace % ALIGN) != 0) return SPGEMM_ERR_INVALID;
-  const int nslabs = slabs_from(opt);
-  const Layout L = layout(A->rows, B->cols, nslabs);
-  if (workspace_bytes < L.total) return SPGEMM_ERR_ALLOC;
+  const int nslabs = slabs_from(opt, B->cols);
+  const Layout L = layout(*A, *B, nslabs, csc);
+  if (workspace_bytes < L.total || fault_is("alloc")) return SPGEMM_ERR_ALLOC;
   cudaStream_t s = (cudaStream_t)stream;
   spgemm_plan_s* p = new (std::nothrow) spgemm_plan_s();
   if (!p) return SPGEMM_ERR_ALLOC;
@@ -206,14 +274,40 @@ spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spg
   p->lim = limits_from(opt);
   p->nslabs = nslabs;
   p->values_mode = (opt && opt->merge_values >= 0 && opt->merge_values <= 2) ? opt->merge_values : 0;
+  p->wopt = wopts_from(opt);
+  p->spin_limit = (opt && opt->debug_spin_limit > 0) ? opt->debug_spin_limit : 0;
+  p->drop_tile = (opt && opt->debug_drop_tile > 0) ? opt->debug_drop_tile - 1 : -1;
   p->L = L;
   p->ws = (unsigned char*)workspace;
   p->ctr = (Counters*)(p->ws + L.ctr);
   cudaMemsetAsync(p->ctr, 0, sizeof(Counters), s);
+  // An operand given by columns is first read as the compressed rows of its transpose (the given
+  // arrays as they are), checked in that form, and transposed into the workspace: its rows in
+  // CSR, with each entry's position in the given arrays (Section IV-A's storage-order conversion).
+  DevCsr given[2] = {p->A, p->B};
+  for (int i = 0; i < 2; ++i) {
+    if (!csc[i]) continue;
+    const spgemm_csr_t* M = i == 0 ? A : B;
+    given[i] = DevCsr{M->cols, M->rows, (long long)M->nnz, M->row_ptr, M->col_idx, nullptr};
+  }
   if (opt && opt->validate) {
     const int grid = num_sms() * 4;
-    if (p->A.rp) k_validate<<<grid, 256, 0, s>>>(p->A, p->ctr);
-    if (p->B.rp) k_validate<<<grid, 256, 0, s>>>(p->B, p->ctr);
+    if (given[0].rp) k_validate<<<grid, 256, 0, s>>>(given[0], p->ctr);
+    if (given[1].rp) k_validate<<<grid, 256, 0, s>>>(given[1], p->ctr);
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (!csc[i]) continue;
+    DevCsr& X = i == 0 ? p->A : p->B;
+    unsigned char* conv = p->ws + L.conv[i];
+    launch_transpose(given[i], conv, p->ctr, s);
+    TransposeView tv = transpose_view(conv, X.rows, X.nnz);
+    X.rp = tv.T_cp;
+    X.col = tv.T_row;
+    X.val = nullptr;
+    p->csc[i] = true;
+    p->perm[i] = tv.T_src;
+    p->cval[i] = (double*)(p->ws + L.cval[i]);
+    p->cgrad[i] = (double*)(p->ws + L.cgrad[i]);
   }
   int* lists[NUM_CLS] = {nullptr, nullptr, (int*)(p->ws + L.list_w), (int*)(p->ws + L.list_b),
                          (int*)(p->ws + L.list_g)};
@@ -238,7 +332,8 @@ spgemm_status_t spgemm_symbolic(spgemm_plan_t p, int32_t* C_row_ptr, int64_t* nn
   cudaStream_t s = (cudaStream_t)stream;
   const Layout& L = p->L;
   const int m = p->A.rows;
-  // scan ticket and tile states start from zero
+  // each structure pass reports its own errors; the scan ticket and tile states start from zero
+  cudaMemsetAsync(&p->ctr->status, 0, sizeof(unsigned), s);
   cudaMemsetAsync(&p->ctr->ticket, 0, sizeof(unsigned), s);
   cudaMemsetAsync(p->ws + L.scan, 0, scan_tile_state_bytes((long long)m + 1), s);
   const int* cnt = p->h.count;
@@ -250,7 +345,8 @@ spgemm_status_t spgemm_symbolic(spgemm_plan_t p, int32_t* C_row_ptr, int64_t* nn
   const int wide = p->h.max_u_merge > 32;
   if (cnt[CLS_M1] + cnt[CLS_M2] > 0) launch_merge_symbolic(wide, p->A, p->B, cls, C_row_ptr, p->ctr, s);
   if (cnt[CLS_W] > 0)
-    launch_hash_symbolic(CLS_W, p->A, p->B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s, p->h.max_u_w);
+    launch_hash_symbolic(CLS_W, p->A, p->B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s, p->h.max_u_w,
+                           p->wopt);
   if (cnt[CLS_B] > 0)
     launch_hash_symbolic(CLS_B, p->A, p->B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s);
   if (cnt[CLS_G] > 0)
@@ -260,7 +356,7 @@ spgemm_status_t spgemm_symbolic(spgemm_plan_t p, int32_t* C_row_ptr, int64_t* nn
   // until a structure pass succeeds, no numeric pass may use a row pointer
   p->state = 1;
   if (read_counters(p, s) != cudaSuccess) return SPGEMM_ERR_CUDA;
-  const spgemm_status_t st = status_from_bits(p->h.status);
+  const spgemm_status_t st = fault_is("nnz_overflow") ? SPGEMM_ERR_OVERFLOW : status_from_bits(p->h.status);
   if (st != SPGEMM_OK) return st;
   p->C_rp = C_row_ptr;
   p->state = 2;
@@ -274,18 +370,18 @@ spgemm_status_t spgemm_numeric(spgemm_plan_t p, const double* A_val, const doubl
   if ((!A_val && p->A.nnz > 0) || (!B_val && p->B.nnz > 0)) return SPGEMM_ERR_INVALID;
   if ((!C_col || !C_val) && p->h.nnzC > 0) return SPGEMM_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
-  DevCsr A = p->A, B = p->B;
-  A.val = A_val;
-  B.val = B_val;
   const Layout& L = p->L;
   const int* cnt = p->h.count;
   uint8_t* cls = p->ws + L.cls;
   const int wide = p->h.max_u_merge > 32;
   if (p->ev_start) cudaEventRecord(p->ev_start, s);
+  DevCsr A, B;
+  prepare_values(p, A_val, B_val, A, B, s);
   if (cnt[CLS_M1] + cnt[CLS_M2] > 0)
     launch_merge_numeric(wide, p->values_mode, A, B, cls, p->C_rp, C_col, C_val, p->ctr, s);
   if (cnt[CLS_W] > 0)
-    launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s, p->h.max_u_w);
+    launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s, p->h.max_u_w,
+                        p->wopt);
   if (cnt[CLS_B] > 0)
     launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], p->C_rp, C_col, C_val, p->ctr, s);
   if (cnt[CLS_G] > 0)
@@ -303,11 +399,11 @@ static spgemm_status_t compute_enqueue(spgemm_plan_t p, const double* A_val, con
   if (!C_row_ptr || capacity < 0) return SPGEMM_ERR_INVALID;
   if ((!A_val && p->A.nnz > 0) || (!B_val && p->B.nnz > 0)) return SPGEMM_ERR_INVALID;
   if ((!C_col || !C_val) && capacity > 0) return SPGEMM_ERR_INVALID;
+  if (fault_is("nnz_overflow")) capacity = 0;
   const Layout& L = p->L;
   const int m = p->A.rows;
   DevCsr A = p->A, B = p->B;
-  A.val = A_val;
-  B.val = B_val;
+  cudaMemsetAsync(&p->ctr->status, 0, sizeof(unsigned), s);   // each structure pass reports its own errors
   if (m == 0) {
     cudaMemsetAsync(C_row_ptr, 0, sizeof(int32_t), s);
     cudaMemsetAsync(&p->ctr->nnzC, 0, sizeof(long long), s);
@@ -322,8 +418,10 @@ static spgemm_status_t compute_enqueue(spgemm_plan_t p, const double* A_val, con
       p->slabs_clean = true;
     }
     if (p->ev_start) cudaEventRecord(p->ev_start, s);
+    prepare_values(p, A_val, B_val, A, B, s);
     if (cnt[CLS_W] > 0)
-      launch_hash_symbolic(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s, p->h.max_u_w);
+      launch_hash_symbolic(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s, p->h.max_u_w,
+                           p->wopt);
     if (cnt[CLS_B] > 0)
       launch_hash_symbolic(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s);
     if (cnt[CLS_G] > 0)
@@ -331,9 +429,10 @@ static spgemm_status_t compute_enqueue(spgemm_plan_t p, const double* A_val, con
                             C_row_ptr, p->ctr, s);
     const int wide = p->h.max_u_merge > 32;
     launch_merge_fused(wide, p->values_mode, A, B, cls, C_row_ptr, C_col, C_val, capacity,
-                       (unsigned long long*)(p->ws + L.fused), p->ctr, s);
+                       (unsigned long long*)(p->ws + L.fused), p->ctr, s, p->spin_limit, p->drop_tile);
     if (cnt[CLS_W] > 0)
-      launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, C_col, C_val, p->ctr, s, p->h.max_u_w);
+      launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, C_col, C_val, p->ctr, s, p->h.max_u_w,
+                        p->wopt);
     if (cnt[CLS_B] > 0)
       launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, C_col, C_val, p->ctr, s);
     if (cnt[CLS_G] > 0)
@@ -402,15 +501,15 @@ spgemm_status_t spgemm_replay(spgemm_plan_t p, const double* A_val, const double
   if ((!A_val && p->A.nnz > 0) || (!B_val && p->B.nnz > 0)) return SPGEMM_ERR_INVALID;
   if ((!C_col || !C_val) && p->h.nnzC > 0) return SPGEMM_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
-  DevCsr A = p->A, B = p->B;
-  A.val = A_val;
-  B.val = B_val;
   const Layout& L = p->L;
   const int* cnt = p->h.count;
   if (p->ev_start) cudaEventRecord(p->ev_start, s);
+  DevCsr A, B;
+  prepare_values(p, A_val, B_val, A, B, s);
   if (cnt[CLS_M1] + cnt[CLS_M2] > 0) launch_replay(p->h.max_u_merge > 32, A, B, p->ws + L.cls, p->C_rp, map, C_val, s);
   if (cnt[CLS_W] > 0)
-    launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s, p->h.max_u_w);
+    launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s, p->h.max_u_w,
+                        p->wopt);
   if (cnt[CLS_B] > 0)
     launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], p->C_rp, C_col, C_val, p->ctr, s);
   if (cnt[CLS_G] > 0)
@@ -439,18 +538,22 @@ spgemm_status_t spgemm_backward(spgemm_plan_t p, const double* A_val, const doub
       return SPGEMM_ERR_ALLOC;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  DevCsr A = p->A, B = p->B;
-  A.val = A_val;
-  B.val = B_val;
   if (p->ev_start) cudaEventRecord(p->ev_start, s);
-  if (dA_val) launch_grad_a(A, B, p->C_rp, p->C_col, dC_val, dA_val, p->ctr, s);
+  DevCsr A, B;
+  prepare_values(p, dB_val ? A_val : nullptr, dA_val ? B_val : nullptr, A, B, s);
+  // gradients of an operand given by columns are formed in row order, then scattered back
+  double* dA_rows = (dA_val && p->csc[0]) ? p->cgrad[0] : dA_val;
+  double* dB_rows = (dB_val && p->csc[1]) ? p->cgrad[1] : dB_val;
+  if (dA_val) launch_grad_a(A, B, p->C_rp, p->C_col, dC_val, dA_rows, p->ctr, s);
   if (dB_val) {
     if (p->transposed_ws != workspace) {
       launch_transpose(A, workspace, p->ctr, s);
       p->transposed_ws = workspace;
     }
-    launch_grad_b(A, B, workspace, p->C_rp, p->C_col, dC_val, dB_val, p->ctr, s);
+    launch_grad_b(A, B, workspace, p->C_rp, p->C_col, dC_val, dB_rows, p->ctr, s);
   }
+  if (dA_rows != dA_val) launch_scatter(p->perm[0], dA_rows, dA_val, p->A.nnz, s);
+  if (dB_rows != dB_val) launch_scatter(p->perm[1], dB_rows, dB_val, p->B.nnz, s);
   if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
   if (cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
   return SPGEMM_OK;

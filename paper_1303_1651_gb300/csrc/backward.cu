@@ -120,22 +120,32 @@ k_grad_b(DevCsr A, DevCsr B, const int* __restrict__ T_cp, const int* __restrict
   if (__any_sync(FULL, miss) && (threadIdx.x & 31) == 0) atomicOr(&ctr->status, ST_MISMATCH);
 }
 
+// Transpose workspace: T_cp (nrows_t + 1), next (nrows_t), T_row (nnz), T_src (nnz), all int, then
+// the scan's tile states; 256-aligned pieces.
+static size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
 size_t transpose_bytes(int nrows_t, long long nnz) {
-  // T_cp (nrows_t + 1), next (nrows_t), T_row (nnz), T_src (nnz), all int, then the scan's tile
-  // states; 256-aligned pieces
-  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-  return up(4 * ((size_t)nrows_t + 1)) + up(4 * (size_t)std::max(nrows_t, 1)) + 2 * up(4 * (size_t)std::max(nnz, 1LL)) +
-         up(scan_tile_state_bytes((long long)nrows_t + 1) + 64);
+  return up256(4 * ((size_t)nrows_t + 1)) + up256(4 * (size_t)std::max(nrows_t, 1)) +
+         2 * up256(4 * (size_t)std::max(nnz, 1LL)) + up256(scan_tile_state_bytes((long long)nrows_t + 1) + 64);
+}
+
+TransposeView transpose_view(void* ws, int nrows_t, long long nnz) {
+  unsigned char* b = (unsigned char*)ws;
+  TransposeView v;
+  v.T_cp = (int*)b;
+  v.T_row = (int*)(b + up256(4 * ((size_t)nrows_t + 1)) + up256(4 * (size_t)std::max(nrows_t, 1)));
+  v.T_src = (int*)((unsigned char*)v.T_row + up256(4 * (size_t)std::max(nnz, 1LL)));
+  return v;
 }
 
 void launch_transpose(const DevCsr& A, void* ws, Counters* ctr, cudaStream_t s) {
-  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
   unsigned char* b = (unsigned char*)ws;
-  int* T_cp = (int*)b;
-  int* next = (int*)(b + up(4 * ((size_t)A.cols + 1)));
-  int* T_row = (int*)((unsigned char*)next + up(4 * (size_t)std::max(A.cols, 1)));
-  int* T_src = (int*)((unsigned char*)T_row + up(4 * (size_t)std::max(A.nnz, 1LL)));
-  unsigned long long* scan_state = (unsigned long long*)((unsigned char*)T_src + up(4 * (size_t)std::max(A.nnz, 1LL)));
+  const TransposeView v = transpose_view(ws, A.cols, A.nnz);
+  int* T_cp = v.T_cp;
+  int* next = (int*)(b + up256(4 * ((size_t)A.cols + 1)));
+  int* T_row = v.T_row;
+  int* T_src = v.T_src;
+  unsigned long long* scan_state = (unsigned long long*)((unsigned char*)T_src + up256(4 * (size_t)std::max(A.nnz, 1LL)));
   cudaMemsetAsync(T_cp, 0, 4 * ((size_t)A.cols + 1), s);
   cudaMemsetAsync(next, 0, 4 * (size_t)std::max(A.cols, 1), s);
   const int grid = num_sms() * 8;
@@ -161,14 +171,41 @@ void launch_grad_a(const DevCsr& A, const DevCsr& B, const int* C_rp, const int*
 void launch_grad_b(const DevCsr& A, const DevCsr& B, const void* tws, const int* C_rp, const int* C_col,
                    const double* W, double* dB, Counters* ctr, cudaStream_t s) {
   if (B.nnz <= 0) return;
-  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-  const unsigned char* b = (const unsigned char*)tws;
-  const int* T_cp = (const int*)b;
-  const int* T_row = (const int*)(b + up(4 * ((size_t)A.cols + 1)) + up(4 * (size_t)std::max(A.cols, 1)));
-  const int* T_src = (const int*)((const unsigned char*)T_row + up(4 * (size_t)std::max(A.nnz, 1LL)));
+  const TransposeView v = transpose_view(const_cast<void*>(tws), A.cols, A.nnz);
+  const int* T_cp = v.T_cp;
+  const int* T_row = v.T_row;
+  const int* T_src = v.T_src;
   const long long need = (B.nnz + BW_THREADS - 1) / BW_THREADS;
   const int grid = (int)std::min<long long>(need, (long long)num_sms() * 16);
   k_grad_b<<<grid, BW_THREADS, 0, s>>>(A, B, T_cp, T_row, T_src, C_rp, C_col, W, dB, ctr);
+}
+
+// Values of an operand given by columns, moved between the given order and the converted row
+// order: gather dst[d] = src[perm[d]], scatter dst[perm[d]] = src[d] (perm is a permutation).
+__global__ void k_gather(const int* __restrict__ perm, const double* __restrict__ src, double* __restrict__ dst,
+                         long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x; d < n; d += stride)
+    dst[d] = __ldg(src + __ldg(perm + d));
+}
+
+__global__ void k_scatter(const int* __restrict__ perm, const double* __restrict__ src, double* __restrict__ dst,
+                          long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x; d < n; d += stride)
+    dst[__ldg(perm + d)] = __ldg(src + d);
+}
+
+void launch_gather(const int* perm, const double* src, double* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  const int grid = (int)std::min<long long>((n + 255) / 256, (long long)num_sms() * 8);
+  k_gather<<<grid, 256, 0, s>>>(perm, src, dst, n);
+}
+
+void launch_scatter(const int* perm, const double* src, double* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  const int grid = (int)std::min<long long>((n + 255) / 256, (long long)num_sms() * 8);
+  k_scatter<<<grid, 256, 0, s>>>(perm, src, dst, n);
 }
 
 }  // namespace spg

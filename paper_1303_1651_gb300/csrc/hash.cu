@@ -321,7 +321,7 @@ __device__ __forceinline__ int warp_max_i(int v) { return __reduce_max_sync(FULL
 template <bool NUM, int U>
 __global__ void __launch_bounds__(WR_WARPS * 32, 1)
 k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __restrict__ rp,
-           int* __restrict__ C_col, double* __restrict__ C_val, Counters* __restrict__ ctr) {
+           int* __restrict__ C_col, double* __restrict__ C_val, Counters* __restrict__ ctr, WarpOrder wo) {
   using L = WarpRowSmem<NUM, U>;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -398,15 +398,29 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
     if (NUM) { g0 = __ldg(rp + r); g1 = __ldg(rp + r + 1); }
     const long long range = (long long)mx - (long long)mn + 1;
     // Choice of ordering (the "Combined" idea of Section IV-B): the bit vector when the column
-    // range is small next to the row (at most 4u words), a register sort when the keys fit 32
-    // bits, a hash table otherwise.  The sort's index takes 7 to 10 bits (by the sort size that
-    // holds u), so its keys fit ranges below 2^25 to 2^22; past 2^22 it is taken only for rows
-    // of more than 32 products: a row of at most 32 products inserts into the hash table in one
-    // step, cheaper there than a sort of 128 keys (measured on random rows of 16 products over
-    // 10^7 columns: 21.0 ms by hash, 25.0 ms by sort).
-    const bool bitvec = range <= WR_RANGE && ((range + 31) >> 5) <= 4 * (long long)u;   // words <= 4u <= RW
+    // range is small next to the row (at most wo.bitvec_ratio columns per product, at most 128,
+    // which is 4u words), a register sort when the keys fit 32 bits, a hash table otherwise.  The
+    // sort's index takes 7 to 10 bits (by the sort size that holds u), so its keys fit ranges
+    // below 2^25 to 2^22; in the automatic choice, past 2^22 it is taken only for rows of more
+    // than 32 products: a row of at most 32 products inserts into the hash table in one step,
+    // cheaper there than a sort of 128 keys (measured on random rows of 16 products over 10^7
+    // columns: 21.0 ms by hash, 25.0 ms by sort).  wo.order forces one of the three where it fits.
+    const bool bv_fits = range <= WR_RANGE && ((range + 31) >> 5) <= 4 * (long long)u;   // words <= 4u <= RW
     const int ib = regsort_index_bits(u <= 128 ? 4 : u <= 256 ? 8 : u <= 512 ? 16 : 32);
-    const bool regsort = !bitvec && (range < (1 << 22) || (u > 32 && range < (1LL << (32 - ib))));
+    const bool rs_fits = range < (1LL << (32 - ib));
+    bool bitvec, regsort;
+    if (wo.order == 1) {
+      bitvec = bv_fits;
+      regsort = !bitvec && rs_fits;
+    } else if (wo.order == 2) {
+      regsort = rs_fits;
+      bitvec = !regsort && bv_fits;
+    } else if (wo.order == 3) {
+      bitvec = regsort = false;
+    } else {
+      bitvec = bv_fits && range <= (long long)wo.bitvec_ratio * u;
+      regsort = !bitvec && (range < (1 << 22) || (u > 32 && rs_fits));
+    }
     if (u > 0 && regsort) {
       int* outc = reinterpret_cast<int*>(reg);
       double* sums = reinterpret_cast<double*>(reg + L::rs_sums);
@@ -545,24 +559,25 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
 
 template <bool NUM, int U>
 static void launch_warp_row_u(const DevCsr& A, const DevCsr& B, const int* list, int count, int* rp, int* C_col,
-                              double* C_val, Counters* ctr, cudaStream_t s) {
+                              double* C_val, Counters* ctr, cudaStream_t s, WarpOrder wo) {
   constexpr size_t bytes = (size_t)WR_WARPS * WarpRowSmem<NUM, U>::bytes;
   auto kern = k_warp_row<NUM, U>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WR_WARPS * 32, bytes);
   const int blocks = std::max(1, std::min((count + WR_WARPS - 1) / WR_WARPS, num_sms() * std::max(per_sm, 1)));
-  kern<<<blocks, WR_WARPS * 32, bytes, s>>>(A, B, list, count, rp, C_col, C_val, ctr);
+  kern<<<blocks, WR_WARPS * 32, bytes, s>>>(A, B, list, count, rp, C_col, C_val, ctr, wo);
 }
 
 // umax: the longest W row (products); the smallest bound U >= umax is launched
 template <bool NUM>
 static void launch_warp_row(const DevCsr& A, const DevCsr& B, const int* list, int count, int umax, int* rp,
-                            int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
+                            int* C_col, double* C_val, Counters* ctr, cudaStream_t s, WarpOrder wo) {
   if (count <= 0) return;
-  if (umax <= 128) launch_warp_row_u<NUM, 128>(A, B, list, count, rp, C_col, C_val, ctr, s);
-  else if (umax <= 256) launch_warp_row_u<NUM, 256>(A, B, list, count, rp, C_col, C_val, ctr, s);
-  else launch_warp_row_u<NUM, WR_UMAX>(A, B, list, count, rp, C_col, C_val, ctr, s);
+  wo.bitvec_ratio = std::max(1, std::min(wo.bitvec_ratio, 128));
+  if (umax <= 128) launch_warp_row_u<NUM, 128>(A, B, list, count, rp, C_col, C_val, ctr, s, wo);
+  else if (umax <= 256) launch_warp_row_u<NUM, 256>(A, B, list, count, rp, C_col, C_val, ctr, s, wo);
+  else launch_warp_row_u<NUM, WR_UMAX>(A, B, list, count, rp, C_col, C_val, ctr, s, wo);
 }
 
 template <int GROUP, int LOG2T, int GPB, bool NUM>
@@ -588,14 +603,14 @@ static void launch_hash(const DevCsr& A, const DevCsr& B, const int* list, int c
 }
 
 void launch_hash_symbolic(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts,
-                          Counters* ctr, cudaStream_t s, int umax) {
-  if (cls == CLS_W) launch_warp_row<false>(A, B, list, count, umax, counts, nullptr, nullptr, ctr, s);
+                          Counters* ctr, cudaStream_t s, int umax, WarpOrder wo) {
+  if (cls == CLS_W) launch_warp_row<false>(A, B, list, count, umax, counts, nullptr, nullptr, ctr, s, wo);
   else launch_hash<512, 13, 1, false>(A, B, list, count, counts, nullptr, nullptr, nullptr, ctr, s);
 }
 
 void launch_hash_numeric(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, const int* rp,
-                         int* C_col, double* C_val, Counters* ctr, cudaStream_t s, int umax) {
-  if (cls == CLS_W) launch_warp_row<true>(A, B, list, count, umax, const_cast<int*>(rp), C_col, C_val, ctr, s);
+                         int* C_col, double* C_val, Counters* ctr, cudaStream_t s, int umax, WarpOrder wo) {
+  if (cls == CLS_W) launch_warp_row<true>(A, B, list, count, umax, const_cast<int*>(rp), C_col, C_val, ctr, s, wo);
   else launch_hash<512, 13, 1, true>(A, B, list, count, nullptr, rp, C_col, C_val, ctr, s);
 }
 

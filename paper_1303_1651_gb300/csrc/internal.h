@@ -26,17 +26,29 @@ void launch_merge_numeric(int wide, int values_mode, const DevCsr& A, const DevC
                           const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s);
 // Fused single pass: numeric for merge-class rows, C's row pointer for every row (rows of other classes
 // bring their counts in rp), entries written into C_col/C_val of `capacity` entries.  Uses ctr->ticket.
+// spin_limit: rounds of re-reads before a look-back gives up (0: the default bound); drop_tile:
+// testing only, a tile that publishes nothing (-1: none).
 void launch_merge_fused(int wide, int values_mode, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* rp,
                         int* C_col, double* C_val, long long capacity, unsigned long long* tile_state, Counters* ctr,
-                        cudaStream_t s);
+                        cudaStream_t s, int spin_limit = 0, int drop_tile = -1);
 size_t fused_tile_state_bytes(int rows);
+
+// Ordering of the rows of class W (the per-row choice of Section IV-B's "Combined" kernel):
+// bitvec_ratio: the bit vector is taken when the row's column range is at most this many columns
+// per product (1..128); order: 0 automatic, 1 bit vector whenever it fits, 2 register sort
+// whenever its keys fit, 3 hash table.
+struct WarpOrder {
+  int bitvec_ratio = 128;
+  int order = 0;
+};
 
 // a2/a4, hash classes W (warp per row) and B (block per row), rows from a list.  umax: the longest
 // W row's products (sizes the W kernel's shared memory); unused for class B.
 void launch_hash_symbolic(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts,
-                          Counters* ctr, cudaStream_t s, int umax = 1024);
+                          Counters* ctr, cudaStream_t s, int umax = 1024, WarpOrder wo = WarpOrder());
 void launch_hash_numeric(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, const int* rp,
-                         int* C_col, double* C_val, Counters* ctr, cudaStream_t s, int umax = 1024);
+                         int* C_col, double* C_val, Counters* ctr, cudaStream_t s, int umax = 1024,
+                         WarpOrder wo = WarpOrder());
 
 // a2/a4, class G: dense accumulator slabs in global memory (one slab per CTA).
 size_t dense_slab_bytes(int ncols);
@@ -45,9 +57,23 @@ void launch_dense_symbolic(const DevCsr& A, const DevCsr& B, const int* list, in
 void launch_dense_numeric(const DevCsr& A, const DevCsr& B, const int* list, int count, void* slabs, int nslabs,
                           const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s);
 
-// Backward: transpose of A's structure (workspace of transpose_bytes(A.cols, A.nnz)), dA, dB.
+// Transpose of A's structure (workspace of transpose_bytes(A.cols, A.nnz)): the compressed rows of
+// A^T -- T_cp (A.cols + 1), T_row (nnz: the row of A of each entry) and T_src (nnz: its position
+// in A) -- each row ordered by (T_row, T_src).  Used by the backward (dB) and to convert an operand
+// given in compressed columns into compressed rows.
 size_t transpose_bytes(int nrows_t, long long nnz);
 void launch_transpose(const DevCsr& A, void* ws, Counters* ctr, cudaStream_t s);
+struct TransposeView {
+  int* T_cp;
+  int* T_row;
+  int* T_src;
+};
+TransposeView transpose_view(void* ws, int nrows_t, long long nnz);
+// dst[d] = src[perm[d]] and dst[perm[d]] = src[d], d < n.
+void launch_gather(const int* perm, const double* src, double* dst, long long n, cudaStream_t s);
+void launch_scatter(const int* perm, const double* src, double* dst, long long n, cudaStream_t s);
+
+// Backward: dA, dB.
 void launch_grad_a(const DevCsr& A, const DevCsr& B, const int* C_rp, const int* C_col, const double* W, double* dA,
                    Counters* ctr, cudaStream_t s);
 void launch_grad_b(const DevCsr& A, const DevCsr& B, const void* tws, const int* C_rp, const int* C_col,

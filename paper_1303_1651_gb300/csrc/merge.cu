@@ -18,10 +18,11 @@
 //                     the tile's product space 32 products at a time; a redux.or of
 //                     run-start bits names each lane's run.  Row t's products are
 //                     contiguous, one slot of skew per row.
-//   3. sort        -- lane t loads keys (column | run rank | product index) into
-//                     registers and runs Batcher's odd-even merge network.  Equal columns end up
-//                     adjacent, in run order and then B order: the order of the
-//                     dense-accumulator loop.
+//   3. sort        -- lane t loads keys (column | product index) into registers and
+//                     runs Batcher's odd-even merge network.  Products are numbered
+//                     run by run, so equal columns end up adjacent, in run order and
+//                     then B order: the order of the dense-accumulator loop.  A
+//                     product's run is the number of run starts at or below its index.
 //   4. count       -- distinct columns of the row (symbolic result).
 //   5. reduce      -- acc = fma(a_rj, b_jx, acc) along each group of equal columns
 //                     in that order, the first product against +0.0.
@@ -36,8 +37,9 @@
 // b_jx from B in the reduce (four positions' loads in flight at a time) and stores
 // each finished entry of C from there; it also reads the columns straight from B when it
 // builds the keys (no expand), so it needs only the run tables in shared memory.
-// Rows of B need not be sorted: the network orders everything.  Keys need
-// column < 2^23 - 1; wider matrices use the hash classes.
+// Rows of B need not be sorted: the network orders everything.  Keys hold the
+// column above 5 or 6 index bits, so B may have at most 2^26 - 2 columns; wider
+// matrices use the hash classes.
 #include "internal.h"
 
 namespace spg {
@@ -91,6 +93,12 @@ __device__ __forceinline__ void oddeven_sort(unsigned (&k)[N]) {
   }
 }
 
+// Rank of the nonempty run holding product idx of a row: bit x of `starts` marks a run that
+// starts at product x (x > 0), so the rank is the number of marks at or below idx.
+__device__ __forceinline__ int run_rank(unsigned long long starts, int idx) {
+  return __popcll(starts & ((2ull << idx) - 1ull));
+}
+
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
@@ -114,35 +122,60 @@ __device__ __forceinline__ int placed_rp(long long pos, int rp_cap) {
   return (int)min(pos, (long long)rp_cap);
 }
 
-__device__ long long tile_lookback(unsigned long long* ts, int tile, long long total, Counters* ctr) {
+// Lane l reads the states of tiles pred - l - 32q, q < LOOKBACK_Q, all in flight together, so a
+// step covers 32 * LOOKBACK_Q predecessors.  Only the states from pred down to the nearest
+// inclusive prefix are needed: those that have published nothing yet are re-read (alone) until
+// they have, the others are not waited for.  The spin bound counts the warp's rounds of re-reads;
+// past it, unresolved states count as an inclusive prefix of 0 and the status reports the timeout.
+// One word per lane measured fastest: 2 and 4 words per lane (64 and 128 predecessors per step)
+// cost more registers and instructions than the round trips they save.
+constexpr int LOOKBACK_Q = 1;
+
+__device__ long long tile_lookback(unsigned long long* ts, int tile, long long total, Counters* ctr,
+                                   long long spin_limit, bool publish) {
   const int lane = threadIdx.x & 31;
   if (tile == 0) return 0;
   long long prefix = 0;
   int pred = tile - 1;
+  long long spins = 0;
   bool timed_out = false;
   while (true) {
-    const int p = pred - lane;
-    unsigned long long w = 2ull;   // before tile 0: an inclusive prefix of 0
-    if (p >= 0) {
-      long long spins = 0;
-      w = ld_volatile_u64(&ts[p]);
-      while ((w & 3ull) == 0ull) {
-        if (++spins > FUSED_SPIN_LIMIT) { timed_out = true; w = 2ull; break; }
-        __nanosleep(32);
-        w = ld_volatile_u64(&ts[p]);
+    unsigned long long w[LOOKBACK_Q];
+#pragma unroll
+    for (int q = 0; q < LOOKBACK_Q; ++q) {
+      const int p = pred - 32 * q - lane;
+      w[q] = p >= 0 ? ld_volatile_u64(&ts[p]) : 2ull;   // before tile 0: an inclusive prefix of 0
+    }
+    unsigned need[LOOKBACK_Q];
+    bool found;
+    while (true) {
+      found = false;
+      unsigned wait[LOOKBACK_Q], any = 0u;
+#pragma unroll
+      for (int q = 0; q < LOOKBACK_Q; ++q) {
+        const unsigned incl = __ballot_sync(FULL, (w[q] & 3ull) == 2ull);
+        need[q] = found ? 0u : (incl ? (0xffffffffu >> (32 - __ffs(incl))) : FULL);
+        found = found || incl != 0u;
+        wait[q] = __ballot_sync(FULL, (w[q] & 3ull) == 0ull) & need[q];
+        any |= wait[q];
       }
+      if (!any) break;
+      const bool give_up = ++spins > spin_limit;
+      timed_out = timed_out || give_up;
+      if (!give_up) __nanosleep(32);
+#pragma unroll
+      for (int q = 0; q < LOOKBACK_Q; ++q)
+        if ((wait[q] >> lane) & 1u) w[q] = give_up ? 2ull : ld_volatile_u64(&ts[pred - 32 * q - lane]);
     }
-    const unsigned incl = __ballot_sync(FULL, (w & 3ull) == 2ull);
-    if (incl) {
-      const int L = __ffs(incl) - 1;          // nearest predecessor with an inclusive prefix
-      prefix += warp_sum_ll(lane <= L ? (long long)(w >> 2) : 0LL);
-      break;
-    }
-    prefix += warp_sum_ll((long long)(w >> 2));
-    pred -= 32;
+    long long part = 0;
+#pragma unroll
+    for (int q = 0; q < LOOKBACK_Q; ++q) part += ((need[q] >> lane) & 1u) ? (long long)(w[q] >> 2) : 0LL;
+    prefix += warp_sum_ll(part);
+    if (found) break;
+    pred -= 32 * LOOKBACK_Q;
   }
-  if (__any_sync(FULL, timed_out) && lane == 0) atomicOr(&ctr->status, ST_TIMEOUT);
-  if (lane == 0) atomicExch(&ts[tile], ((unsigned long long)(prefix + total) << 2) | 2ull);
+  if (timed_out && lane == 0) atomicOr(&ctr->status, ST_TIMEOUT);
+  if (publish && lane == 0) atomicExch(&ts[tile], ((unsigned long long)(prefix + total) << 2) | 2ull);
   return prefix;
 }
 
@@ -156,14 +189,16 @@ struct MergeArgs {
   unsigned long long* tile_state;
   Counters* ctr;
   int rp_cap;                    // FUSED: min(capacity, INT_MAX), the largest row pointer entry stored
+  long long spin_limit;          // FUSED: rounds of re-reads before a look-back gives up
+  int drop_tile;                 // FUSED, testing: a tile that publishes nothing (-1: none)
 };
 
-template <int MODE, int N, int WARPS, bool DIRECT>
+template <int MODE, int N, int WARPS, bool DIRECT, bool RK>
 __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigned char* wb) {
   using L = SortSmem<MODE, N, DIRECT>;
   constexpr bool V = L::V;
   constexpr int IB = (N == 32) ? 5 : 6;     // product-index bits of a key
-  constexpr int KB = IB + 3;                // + run-index bits: key = col << KB | run << IB | index
+  constexpr int KB = RK ? IB + 3 : IB;      // key = col << KB | (RK: run rank << IB) | index
   constexpr unsigned PAD = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   double* s_val = reinterpret_cast<double*>(wb + L::s_val);
@@ -280,11 +315,11 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       const unsigned rj = (unsigned)__popcll(starts & ((2ull << j) - 1ull));
+      const unsigned rk = RK ? (rj << IB) : 0u;
       if constexpr (DIRECT)   // column straight from B: all N loads of the lane in flight together
-        key[j] = (j < u) ? (((unsigned)__ldg(B.col + s_bofs[rj * 32 + lane] + j) << KB) | (rj << IB) | (unsigned)j)
-                         : PAD;
+        key[j] = (j < u) ? (((unsigned)__ldg(B.col + s_bofs[rj * 32 + lane] + j) << KB) | rk | (unsigned)j) : PAD;
       else
-        key[j] = (j < u) ? ((s_col[base + j] << KB) | (rj << IB) | (unsigned)j) : PAD;
+        key[j] = (j < u) ? ((s_col[base + j] << KB) | rk | (unsigned)j) : PAD;
     }
   }
   __syncwarp();   // every lane has its keys: s_col may now be overwritten
@@ -307,7 +342,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
   const int mycount = mine ? cnt : other;
   int TA = 0;
   const int oa = (MODE == MODE_FUSED) ? warp_excl_scan(mycount, &TA) : 0;
-  if (MODE == MODE_FUSED) tile_publish(g.tile_state, tile, TA);
+  if (MODE == MODE_FUSED && tile != g.drop_tile) tile_publish(g.tile_state, tile, TA);
 
   if constexpr (DIRECT) {
     // 5'. place first (the offset in C is needed to store from the reduce), then reduce: values
@@ -322,7 +357,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
       const int mycount = mine ? cnt : other;
       int TA;
       const int oa = warp_excl_scan(mycount, &TA);
-      const long long off = tile_lookback(g.tile_state, tile, TA, g.ctr);
+      const long long off = tile_lookback(g.tile_state, tile, TA, g.ctr, g.spin_limit, tile != g.drop_tile);
       gstart = off + oa;
       if (inrange) {
         if (gstart + mycount > g.rp_cap) atomicOr(&g.ctr->status, ST_OVERFLOW);
@@ -354,7 +389,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
           bb[q] = 0.0; aa[q] = 0.0;
           if (j + q < umax && kq != PAD) {
             const int idx = (int)(kq & (unsigned)(N - 1));
-            const int run = (int)((kq >> IB) & 7u);
+            const int run = RK ? (int)((kq >> IB) & 7u) : run_rank(starts, idx);
             bb[q] = __ldg(B.val + s_bofs[run * 32 + lane] + idx);
             aa[q] = s_a[run * 32 + lane];
           }
@@ -395,7 +430,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
         const unsigned kj = key[j];
         const bool valid = kj != PAD;
         const int idx = (int)(kj & (unsigned)(N - 1));
-        const int run = (int)((kj >> IB) & 7u);
+        const int run = RK ? (int)((kj >> IB) & 7u) : run_rank(starts, idx);
         double a = 0.0, b = 0.0;
         if (valid) {
           b = s_val[base + idx];
@@ -424,7 +459,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
     lim = gend - gbeg;
     if (mine && lim != cnt) atomicOr(&g.ctr->status, ST_MISMATCH);
   } else {
-    const long long off = tile_lookback(g.tile_state, tile, TA, g.ctr);
+    const long long off = tile_lookback(g.tile_state, tile, TA, g.ctr, g.spin_limit, tile != g.drop_tile);
     gstart = off + oa;
     if (inrange) {
       if (gstart + mycount > g.rp_cap) atomicOr(&g.ctr->status, ST_OVERFLOW);
@@ -545,7 +580,7 @@ __device__ __forceinline__ void merge_tile_pair(const MergeArgs& g, int tile, un
   constexpr bool V = L::V;
   constexpr int H = 32;                     // sorted positions per lane
   constexpr int IB = 6;                     // product-index bits of a key
-  constexpr int KB = IB + 3;                // key = col << KB | run << IB | index
+  constexpr int KB = IB;                    // key = col << KB | index
   constexpr unsigned PAD = 0xffffffffu;
   const int lane = threadIdx.x & 31, t = lane >> 1, h = lane & 1;
   double* s_val = reinterpret_cast<double*>(wb + L::s_val);
@@ -654,8 +689,7 @@ __device__ __forceinline__ void merge_tile_pair(const MergeArgs& g, int tile, un
 #pragma unroll
     for (int j = 0; j < H; ++j) {
       const int x = H * h + ((j + 16 * h) & (H - 1));   // lane 2t+1 rotated by 16: the pair reads different banks
-      const unsigned rj = (unsigned)__popcll(starts & ((2ull << x) - 1ull));
-      key[j] = (x < u) ? ((s_col[base + x] << KB) | (rj << IB) | (unsigned)x) : PAD;
+      key[j] = (x < u) ? ((s_col[base + x] << KB) | (unsigned)x) : PAD;
     }
   }
   __syncwarp();   // every lane has its keys: s_col may now be overwritten
@@ -693,7 +727,7 @@ __device__ __forceinline__ void merge_tile_pair(const MergeArgs& g, int tile, un
   const int mycount = h == 0 ? (mine ? cnt : other) : 0;
   int TA = 0;
   const int oa = (MODE == MODE_FUSED) ? warp_excl_scan(mycount, &TA) : 0;
-  if (MODE == MODE_FUSED) tile_publish(g.tile_state, tile, TA);
+  if (MODE == MODE_FUSED && tile != g.drop_tile) tile_publish(g.tile_state, tile, TA);
 
   // 5. reduce, pass 1: each lane's chains; a continued first group (cont0) is left for pass 2
   const bool next_cont = __shfl_xor_sync(FULL, cont0 ? 1 : 0, 1) != 0 && h == 0;   // lane 2t: last group goes on
@@ -713,7 +747,7 @@ __device__ __forceinline__ void merge_tile_pair(const MergeArgs& g, int tile, un
         const unsigned kj = key[j];
         const bool valid = kj != PAD;
         const int idx = (int)(kj & 63u);
-        const int run = (int)((kj >> IB) & 7u);
+        const int run = run_rank(starts, idx);
         double a = 0.0, b = 0.0;
         if (valid) {
           b = s_val[base + idx];
@@ -745,7 +779,7 @@ __device__ __forceinline__ void merge_tile_pair(const MergeArgs& g, int tile, un
         if (j < glen) {
           const unsigned kj = key[j];
           const int idx = (int)(kj & 63u);
-          const int run = (int)((kj >> IB) & 7u);
+          const int run = run_rank(starts, idx);
           acc2 = __fma_rn(s_a[run * L::ROWS + t], s_val[base + idx], acc2);
           if (j == glen - 1) {
             s_col[base + ends_lo] = kj;
@@ -765,7 +799,7 @@ __device__ __forceinline__ void merge_tile_pair(const MergeArgs& g, int tile, un
     lim = gend - gbeg;
     if (mine && h == 0 && lim != cnt) atomicOr(&g.ctr->status, ST_MISMATCH);
   } else {
-    const long long off = tile_lookback(g.tile_state, tile, TA, g.ctr);
+    const long long off = tile_lookback(g.tile_state, tile, TA, g.ctr, g.spin_limit, tile != g.drop_tile);
     gstart = off + oa_row;
     if (inrange && h == 0) {
       const int rowcount = mine ? cnt : other;
@@ -857,7 +891,7 @@ static void launch_merge_pair(const MergeArgs& g, cudaStream_t s) {
 
 // The fused direct form with 32-product tiles runs best with 28 warps of at most 72 registers
 // (a few spill to L1); the other forms keep their natural register counts.
-template <int MODE, int N, int WARPS, bool DIRECT>
+template <int MODE, int N, int WARPS, bool DIRECT, bool RK>
 __global__ void __launch_bounds__(WARPS * 32, (N == 32 && DIRECT && MODE == MODE_FUSED) ? 28 : 1)
 k_merge(MergeArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -866,7 +900,7 @@ k_merge(MergeArgs g) {
   const int ntiles = (g.A.rows + 31) >> 5;
   if (MODE != MODE_FUSED) {
     for (int tile = blockIdx.x * WARPS + warp; tile < ntiles; tile += gridDim.x * WARPS) {
-      merge_tile<MODE, N, WARPS, DIRECT>(g, tile, wb);
+      merge_tile<MODE, N, WARPS, DIRECT, RK>(g, tile, wb);
       __syncwarp();
     }
   } else {
@@ -877,7 +911,7 @@ k_merge(MergeArgs g) {
       if (lane == 0) tile = (int)atomicAdd(&g.ctr->ticket, 1u);
       tile = __shfl_sync(FULL, tile, 0);
       if (tile >= ntiles) break;
-      merge_tile<MODE, N, WARPS, DIRECT>(g, tile, wb);
+      merge_tile<MODE, N, WARPS, DIRECT, RK>(g, tile, wb);
       __syncwarp();
     }
   }
@@ -886,7 +920,11 @@ k_merge(MergeArgs g) {
 template <int MODE, int N, int WARPS, bool DIRECT = false>
 static void launch_merge(const MergeArgs& g, cudaStream_t s) {
   constexpr size_t bytes = (size_t)WARPS * SortSmem<MODE, N, DIRECT>::bytes;
-  auto kern = k_merge<MODE, N, WARPS, DIRECT>;
+  // The 32-product direct form also keeps the run rank in its keys (one shift instead of a
+  // popcount per position of the reduce) while the column fits above 8 bits: B.cols <= 2^24 - 2.
+  constexpr bool RK_FORM = N == 32 && DIRECT;
+  auto kern = (RK_FORM && g.B.cols <= (1 << 24) - 2) ? k_merge<MODE, N, WARPS, DIRECT, RK_FORM>
+                                                      : k_merge<MODE, N, WARPS, DIRECT, false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   const int ntiles = (g.A.rows + 31) / 32;
   int per_sm = 0;
@@ -901,21 +939,21 @@ static void launch_merge(const MergeArgs& g, cudaStream_t s) {
   kern<<<blocks, WARPS * 32, bytes, s>>>(g);
 }
 
-int merge_max_cols() { return (1 << 23) - 2; }
+int merge_max_cols() { return (1 << 26) - 2; }
 
 // tiles of 32 rows, or of 16 in the two-lanes-per-row form
 size_t fused_tile_state_bytes(int rows) { return (size_t)((rows + 15) / 16) * sizeof(unsigned long long); }
 
 void launch_merge_symbolic(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* counts,
                            Counters* ctr, cudaStream_t s) {
-  MergeArgs g{A, B, rowcls, counts, nullptr, nullptr, 0, nullptr, ctr};
+  MergeArgs g{A, B, rowcls, counts, nullptr, nullptr, 0, nullptr, ctr, 0, 0, -1};
   if (!wide) launch_merge<MODE_SYM, 32, 4>(g, s);
   else launch_merge<MODE_SYM, 64, 4>(g, s);
 }
 
 void launch_merge_numeric(int wide, int values_mode, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls,
                           const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
-  MergeArgs g{A, B, rowcls, const_cast<int*>(rp), C_col, C_val, 0, nullptr, ctr};
+  MergeArgs g{A, B, rowcls, const_cast<int*>(rp), C_col, C_val, 0, nullptr, ctr, 0, 0, -1};
   const bool direct = values_mode == 1 || (values_mode == 0 && !wide);
   if (direct) {
     if (!wide) launch_merge<MODE_NUM, 32, 1, true>(g, s);
@@ -928,9 +966,10 @@ void launch_merge_numeric(int wide, int values_mode, const DevCsr& A, const DevC
 
 void launch_merge_fused(int wide, int values_mode, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* rp,
                         int* C_col, double* C_val, long long capacity, unsigned long long* tile_state, Counters* ctr,
-                        cudaStream_t s) {
+                        cudaStream_t s, int spin_limit, int drop_tile) {
   MergeArgs g{A, B, rowcls, rp, C_col, C_val, capacity, tile_state, ctr,
-              (int)std::min(capacity, (long long)INT_MAX)};
+              (int)std::min(capacity, (long long)INT_MAX), spin_limit > 0 ? (long long)spin_limit : FUSED_SPIN_LIMIT,
+              drop_tile};
   const bool direct = values_mode == 1 || (values_mode == 0 && !wide);
   if (direct) {
     if (!wide) launch_merge<MODE_FUSED, 32, 1, true>(g, s);

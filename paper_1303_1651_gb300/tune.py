@@ -20,17 +20,40 @@ import torch
 
 from . import binding
 
+# Each candidate belongs to one group of knobs; the best of each group are also tried together.
 CANDIDATES = [
     {},                                           # defaults: M1 <= 32, M2 <= 64, W <= 1024, B <= 4096
-    {"merge_values": 1},                          # sort classes: direct form (read from B)
-    {"merge_values": 2},                          # sort classes: staged form
-    {"m2_max_u": 32, "merge_values": 1},
-    {"m2_max_u": 32},                             # 33..64-product rows to the warp hash (32-product tiles)
+    # sort classes: tile size and value path
+    {"merge_values": 1},                          # direct form (values read from B, C from the reduce)
+    {"merge_values": 2},                          # staged form (values copied with the tile)
+    {"m2_max_u": 32, "merge_values": 1},          # 32-row tiles only: 33..64-product rows to class W
+    {"m2_max_u": 32},
     {"m1_max_u": 16, "m2_max_u": 32},
     {"merge_max_k": 4},
+    {"m1_max_u": -1, "m2_max_u": -1},             # no sort classes: every row to the warp and block classes
+    # class limits (bins): rows per warp / per block before the dense accumulator
     {"warp_max_u": 256},
-    {"m1_max_u": -1, "m2_max_u": -1},             # no sort classes: hash everything
+    {"warp_max_u": 512},
+    {"block_max_u": 2048},
+    # class W: the per-row ordering (Section IV-B's "Combined" switch and its alternatives)
+    {"warp_bitvec_ratio": 2},                     # the paper's rule: range below twice the row
+    {"warp_bitvec_ratio": 32},
+    {"warp_order": 2},                            # register sort wherever its keys fit
+    {"warp_order": 3},                            # hash table always
 ]
+
+GROUPS = {
+    "sort": ("merge_values", "m1_max_u", "m2_max_u", "merge_max_k"),
+    "bins": ("warp_max_u", "block_max_u"),
+    "warp": ("warp_bitvec_ratio", "warp_order"),
+}
+
+
+def group_of(c: dict) -> str | None:
+    for g, keys in GROUPS.items():
+        if c and all(k in keys for k in c):
+            return g
+    return None
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "spgemm_gb300_tune.json")
 
@@ -80,12 +103,29 @@ def tune(A: binding.DeviceCSR, B: binding.DeviceCSR, candidates=None, reps: int 
     if not refresh and key in cache:
         return cache[key]
     trials = []
-    for c in candidates:
+
+    def trial(c):
         try:
             trials.append({"options": c, "ms": _time(A, B, c, reps)})
         except binding.SpgemmError as e:
             trials.append({"options": c, "ms": None, "error": e.name})
+
+    for c in candidates:
+        trial(c)
     ok = [t for t in trials if t["ms"] is not None]
+    base = next((t["ms"] for t in ok if not t["options"]), None)
+    # the best candidate of each group that beat the defaults, tried together
+    winners = {}
+    for t in ok:
+        g = group_of(t["options"])
+        if g and (base is None or t["ms"] < base) and (g not in winners or t["ms"] < winners[g]["ms"]):
+            winners[g] = t
+    if len(winners) > 1:
+        merged = {}
+        for t in winners.values():
+            merged.update(t["options"])
+        trial(merged)
+        ok = [t for t in trials if t["ms"] is not None]
     best = min(ok, key=lambda t: t["ms"])
     result = {"options": best["options"], "ms": best["ms"], "trials": trials}
     if cache_path:

@@ -95,3 +95,34 @@ def test_struct_sizes_match_header(lib):
     assert ctypes.sizeof(binding.spgemm_options_t) == 64
     assert ctypes.sizeof(binding.spgemm_csr_t) == 40
     assert ctypes.sizeof(binding.spgemm_info_t) == 40
+
+
+def test_options_fields_follow_the_header():
+    # the ctypes mirror lists spgemm_options_t's fields in the header's order
+    text = open(os.path.join(ROOT, "include", "spgemm_gb300.h")).read()
+    body = text[text.index("typedef struct {\n  int32_t merge_max_k;"):]
+    body = body[:body.index("} spgemm_options_t;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"int32_t\s+([a-z0-9_]+)", body)
+    assert names == [f[0] for f in binding.spgemm_options_t._fields_]
+
+
+def test_storage_options_checked_on_host(lib):
+    A, B = _desc(1000, 500, 10), _desc(500, 700, 10)
+    plain, csc = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    assert lib.spgemm_workspace_size(ctypes.byref(A), ctypes.byref(B), None, ctypes.byref(plain)) == 0
+    opt = binding.options(a_storage=1, b_storage=1)
+    assert lib.spgemm_workspace_size(ctypes.byref(A), ctypes.byref(B), ctypes.byref(opt), ctypes.byref(csc)) == 0
+    assert csc.value > plain.value           # the converted structures, values and gradients
+    bad = binding.options(b_storage=2)
+    assert lib.spgemm_workspace_size(ctypes.byref(A), ctypes.byref(B), ctypes.byref(bad), ctypes.byref(csc)) == 1
+    # a descriptor given by columns needs its column pointers
+    A_cols = binding.spgemm_csr_t(0, 500, 0, None, None, None)
+    assert lib.spgemm_workspace_size(ctypes.byref(A_cols), ctypes.byref(B), ctypes.byref(opt), ctypes.byref(csc)) == 1
+
+
+def test_fault_injection_alloc_on_host(lib, monkeypatch):
+    A, B = _desc(10, 5, 3), _desc(5, 7, 3)
+    h = ctypes.c_void_p(0)
+    monkeypatch.setenv("SPGEMM_FAULT", "alloc")
+    assert lib.spgemm_plan(ctypes.byref(h), ctypes.byref(A), ctypes.byref(B), None, 0x100000, 1 << 40, None) == 2

@@ -52,3 +52,39 @@ def test_per_matrix_path_matches_batched():
     pm = batched.PerMatrix(devp)
     pm.run()
     assert pm.F == sum(oracle.flops(Ap, Bp) for Ap, Bp in probs)
+
+
+def test_tuned_batch_matches_oracle_per_problem():
+    # the autotuner's choice (whatever it is) must leave every problem's product unchanged
+    from paper_1303_1651_gb300 import tune
+    probs = synth.batch_problems(count=24, seed=12, nmin=64, nmax=4000)
+    A, B, lay = batched.concat(probs)
+    dA, dB = binding.DeviceCSR.from_host(A), binding.DeviceCSR.from_host(B)
+    tuned = tune.tune(dA, dB, reps=1, cache_path=None)
+    assert len(tuned["trials"]) >= len(tune.CANDIDATES)
+    opt = binding.options(**tuned["options"]) if tuned["options"] else None
+    bp = batched.BatchedProduct(dA, dB, opt)
+    bp.run()
+    torch.cuda.synchronize()
+    bp.check()
+    got = bp.result_host()
+    for p, (Ap, Bp) in enumerate(probs):
+        compare(batched.split(got, lay, p), oracle.spgemm(Ap, Bp), single=True)
+    bp.close()
+
+
+@pytest.mark.parametrize("cand", list(range(16)))
+def test_every_tuner_candidate_matches_oracle(cand):
+    from paper_1303_1651_gb300 import tune
+    if cand >= len(tune.CANDIDATES):
+        pytest.skip("fewer candidates")
+    probs = small_batch(seed=13, count=12)
+    A, B, lay = batched.concat(probs)
+    dA, dB = binding.DeviceCSR.from_host(A), binding.DeviceCSR.from_host(B)
+    c = tune.CANDIDATES[cand]
+    bp = batched.BatchedProduct(dA, dB, binding.options(**c) if c else None)
+    bp.run()
+    torch.cuda.synchronize()
+    bp.check()
+    compare(bp.result_host(), oracle.spgemm(A, B), single=True)
+    bp.close()

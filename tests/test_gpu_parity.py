@@ -266,14 +266,15 @@ def test_fused_then_numeric_with_new_values():
                          ids=["bitvector", "regsort-256", "regsort-1024", "regsort-128-range-2^25",
                               "regsort-256-range-2^24", "hash-256", "hash-1024", "hash-16-range-2^25"])
 def test_warp_class_orderings(ncols, k, fused):
-    # rows of k entries of A times rows of k entries of B: u = k^2 products, warp class W;
-    # the column range of B picks the ordering (bit vector / register sort / hash table).  The
-    # register sort's keys hold the column offset above a 7- to 10-bit product index (by the sort
-    # size that holds u), so it takes ranges below 2^25 (u <= 128) down to 2^22 (u <= 1024); past
-    # 2^22 only rows of more than 32 products take it.
+    # rows of k entries of A times rows of k entries of B: u = k^2 products, warp class W (the
+    # sort classes are switched off, so the rows of 16 products go there too); the column range
+    # of B picks the ordering (bit vector / register sort / hash table).  The register sort's keys
+    # hold the column offset above a 7- to 10-bit product index (by the sort size that holds u),
+    # so it takes ranges below 2^25 (u <= 128) down to 2^22 (u <= 1024); past 2^22 only rows of
+    # more than 32 products take it.
     A = synth.random_k(700, k, 81, ncols=400)
     B = synth.random_k(400, k, 82, ncols=ncols)
-    C = gpu_product(A, B, fused=fused)
+    C = gpu_product(A, B, opts(m1_max_u=-1, m2_max_u=-1), fused=fused)
     assert C["info"]["rows_per_class"]["W"] == 700
     compare(C, oracle.spgemm(A, B), single=True)
 
@@ -316,3 +317,28 @@ def test_more_live_plans_than_pinned_slots():
         compare(prod.numeric().to_host(), R, single=True)
     finally:
         prod.close()
+
+
+@PATHS
+@pytest.mark.parametrize("ncols,k", [(9_000_000, 4), (30_000_000, 5), (30_000_000, 8), ((1 << 26) - 2, 6)],
+                         ids=["M1-9e6", "M1-3e7", "M2-3e7", "M2-limit"])
+def test_sort_classes_wide_b(ncols, k, fused):
+    # B wider than 2^23 columns: the sort keys hold the column above the 5- or 6-bit product index
+    # only, so the sort classes take every B up to 2^26 - 2 columns
+    A = synth.random_k(3000, k, 71, ncols=500)
+    B = synth.random_k(500, k, 72, ncols=ncols)
+    C = gpu_product(A, B, fused=fused)
+    cls = C["info"]["rows_per_class"]
+    assert cls["M1"] + cls["M2"] == 3000, cls
+    compare(C, oracle.spgemm(A, B), single=True)
+
+
+@PATHS
+def test_sort_classes_off_past_limit(fused):
+    # one column more than the keys hold: every row goes to the warp class, same product
+    A = synth.random_k(1000, 4, 73, ncols=300)
+    B = synth.random_k(300, 4, 74, ncols=(1 << 26) - 1)
+    C = gpu_product(A, B, fused=fused)
+    cls = C["info"]["rows_per_class"]
+    assert cls["M1"] + cls["M2"] == 0 and cls["W"] == 1000, cls
+    compare(C, oracle.spgemm(A, B), single=True)
