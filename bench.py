@@ -44,12 +44,14 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "medium", "batched16"],
-                    help="plain: the benchmark workload; medium: Laplacian 1024^2 + random 500K x 8 "
+    ap.add_argument("--workload", default="plain", choices=["plain", "medium", "small", "batched16"],
+                    help="plain: the benchmark workload; small: Laplacian 64^2 + random 4096 x 8 (the small "
+                         "case); medium: Laplacian 1024^2 + random 500K x 8 "
                          "(inputs above L2, a few hundred MB; for profiler captures); batched16: the first "
                          "16 random x random problems of the batched workload as one block-diagonal product "
                          "(for captures of the warp-per-row class)")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched, backward and long-row measurements")
+    ap.add_argument("--no-parity", action="store_true", help="skip the full-size check against the oracle")
     ap.add_argument("--sweep", action="store_true",
                     help="time the size sweep instead (13 log-spaced N from 1e3 to 1e7 for the Laplacian^2 and "
                          "random*random at 4, 8 and 16 per row; one JSON line with a row per point)")
@@ -63,6 +65,10 @@ def make_workload(kind: str = "plain"):
         probs = synth.batch_problems(count=512, seed=synth.SEED_BATCH)[256:272]
         A, B, _ = batched.concat(probs)
         return [("batched16_random", A, B)]
+    if kind == "small":
+        L = synth.laplacian5(64)
+        return [("laplacian5_64_sq", L, L), ("random_4096_k8", synth.random_k(4096, 8, synth.SEED_A),
+                                             synth.random_k(4096, 8, synth.SEED_B))]
     if kind == "medium":
         L = synth.laplacian5(1024)
         R1 = synth.random_k(500_000, 8, synth.SEED_A)
@@ -194,6 +200,133 @@ def oracle_rate(work, frac: float, reps: int = 1):
             F += oracle.spgemm(As, B)["F"]
     dt = time.perf_counter() - t0
     return 2 * F / dt / 1e9, dt, F
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_protocol(work, frac: float, min_s: float = 2.0, min_runs: int = 5, max_s: float = 15.0) -> dict:
+    """The oracle on one host thread, on the first frac of the rows of each product, repeated until
+    at least min_s seconds and min_runs runs (the paper's protocol, Section III): best and median."""
+    rates, total = [], 0.0
+    F = 0
+    while (total < min_s or len(rates) < min_runs) and total < max_s:
+        r, dt, F = oracle_rate(work, frac)
+        rates.append(r)
+        total += dt
+    return {"value": max(rates), "median": float(np.median(rates)), "unit": "GFLOP/s", "cores": 1, "threads": 1,
+            "kind": "oracle", "runs": len(rates), "seconds": round(total, 2), "cpu_model": cpu_model(),
+            "sample": f"first {frac:.4g} of the rows of A in each product, full B ({F} products per run); "
+                      f"best of {len(rates)} runs"}
+
+
+# Worker side of the multi-process oracle: each worker builds the (seeded) workload once.
+_WORK = {}
+
+
+def _worker_work(kind):
+    if kind not in _WORK:
+        _WORK.clear()
+        _WORK[kind] = make_workload(kind)
+    return _WORK[kind]
+
+
+def _oracle_rows(kind, i, r0, r1):
+    """Oracle product of rows r0..r1 of product i of the workload: (products, seconds)."""
+    import oracle
+    _, A, B = _worker_work(kind)[i]
+    As = row_block(A, r0, r1)
+    t0 = time.perf_counter()
+    F = oracle.spgemm(As, B)["F"]
+    return F, time.perf_counter() - t0
+
+
+def _oracle_check_rows(kind, name, r0, r1, rp, col, val):
+    """Rows r0..r1 of the named product computed on the GPU (rp relative to its first entry) against
+    the oracle: (pattern equal, max |c - c_ref| / sum|a b|, max plain relative error over c_ref != 0)."""
+    import oracle
+    _, A, B = next(w for w in _worker_work(kind) if w[0] == name)
+    R = oracle.spgemm(row_block(A, r0, r1), B)
+    same = np.array_equal(np.asarray(rp, np.int64), R["row_ptr"]) and np.array_equal(np.asarray(col, np.int64),
+                                                                                     R["col_idx"])
+    if not same:
+        return False, float("inf"), float("inf")
+    diff = np.abs(np.asarray(val) - R["val"])
+    gate = float((diff / np.where(R["absval"] > 0, R["absval"], 1.0)).max(initial=0.0))
+    nz = R["val"] != 0
+    plain = float((diff[nz] / np.abs(R["val"][nz])).max(initial=0.0))
+    return True, gate, plain
+
+
+def row_block(A, r0: int, r1: int):
+    """Rows r0..r1-1 of A (all its columns)."""
+    e0, e1 = int(A.row_ptr[r0]), int(A.row_ptr[r1])
+    return synth.CSR(r1 - r0, A.cols, (A.row_ptr[r0:r1 + 1] - e0).astype(np.int32), A.col_idx[e0:e1].copy(),
+                     A.val[e0:e1].copy())
+
+
+def chunks(rows: int, n: int):
+    step = max(1, -(-rows // n))
+    return [(r, min(rows, r + step)) for r in range(0, rows, step)]
+
+
+def spawn_pool(workers: int):
+    """A process pool started with spawn (safe after CUDA has been initialised in this process)."""
+    import multiprocessing
+    from concurrent.futures import ProcessPoolExecutor
+    return ProcessPoolExecutor(workers, mp_context=multiprocessing.get_context("spawn"))
+
+
+def oracle_all_cores(kind, work, workers: int, min_s: float = 2.0, min_runs: int = 5, max_s: float = 20.0) -> dict:
+    """The oracle over the whole workload on every host core: rows split into chunks, one process
+    per core; best and median wall time of repeated runs."""
+    jobs = [(kind, i, r0, r1) for i, (_, A, _) in enumerate(work) for r0, r1 in chunks(A.rows, 4 * workers)]
+    rates, total, F = [], 0.0, 0
+    with spawn_pool(workers) as ex:
+        list(ex.map(_worker_work, [kind] * (4 * workers)))      # every worker builds the workload once
+        while (total < min_s or len(rates) < min_runs) and total < max_s:
+            t0 = time.perf_counter()
+            F = sum(f for f, _ in ex.map(_oracle_rows, *zip(*jobs)))
+            dt = time.perf_counter() - t0
+            rates.append(2 * F / dt / 1e9)
+            total += dt
+    return {"value": max(rates), "median": float(np.median(rates)), "unit": "GFLOP/s", "cores": workers,
+            "threads": workers, "kind": "oracle, one process per host core over row chunks", "runs": len(rates),
+            "cpu_model": cpu_model(), "sample": f"the whole workload ({F} products per run); best of {len(rates)} runs"}
+
+
+def check_full_products(kind, results, workers: int) -> dict:
+    """Every entry of the full-size products against the oracle (rows in chunks over the host cores):
+    pattern bit-exact, the gate max |c - c_ref| / sum|a b|, and the plain max relative error."""
+    out = {}
+    with spawn_pool(workers) as ex:
+        for name, rp, col, val in results:
+            jobs = []
+            for r0, r1 in chunks(len(rp) - 1, 4 * workers):
+                e0, e1 = int(rp[r0]), int(rp[r1])
+                jobs.append(ex.submit(_oracle_check_rows, kind, name, r0, r1, rp[r0:r1 + 1] - e0, col[e0:e1],
+                                      val[e0:e1]))
+            res = [j.result() for j in jobs]
+            out[name] = {"pattern_equal": all(r[0] for r in res),
+                         "max_err_over_sum_abs": max(r[1] for r in res),
+                         "max_plain_rel_err": max(r[2] for r in res), "entries": int(rp[-1])}
+    return out
 
 
 def combined_rate(work, threads: int, frac: float = 1.0):
@@ -333,6 +466,7 @@ def run_ours(args, rank, world, local_rank):
             nnz = binding.spgemm_compute(plan, p["dA"].val, p["dB"].val, p["C_rp"], C_col, C_val, stream)
             p["info"] = info
             p["nnz"] = nnz
+            p["last_C"] = (C_col, C_val)
         finally:
             binding.spgemm_free(plan)
         return C_col, C_val
@@ -379,6 +513,15 @@ def run_ours(args, rank, world, local_rank):
         t1.record(stream)
         barrier()
     ms = ranks.max_over_ranks(t0.elapsed_time(t1) / args.steps, dist, dev)
+    # the last timed step's C, kept for the full-size check against the oracle (after all timing)
+    if rank == 0 and world == 1 and not args.no_parity:
+        for p in prods:
+            C_col, C_val = p["last_C"]
+            nnz = p["nnz"]
+            p["C_host"] = (p["C_rp"].cpu().numpy().astype(np.int64), C_col[:nnz].cpu().numpy(),
+                           C_val[:nnz].cpu().numpy())
+    for p in prods:
+        p.pop("last_C", None)
 
     # the three-call path (plan / symbolic / numeric) on the same inputs, for comparison
     for _ in range(2):
@@ -439,17 +582,27 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the C ABI from pinned host buffers
     e2e = run_e2e(args, prods, dev, stream, binding, torch, world, dist)
 
-    cpu = cpu_combined = None
+    cpu = cpu_combined = cpu_all = parity = None
     if rank == 0 and world == 1:
-        rate, dt, F = oracle_rate(work, 1.0 / 16)
-        cpu = {"value": rate, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": f"first 1/16 of the rows of A in each product, full B ({dt:.1f} s, {F} products)"}
+        workers = max(1, min(os.cpu_count() or 1, 64))
+        cpu = oracle_protocol(work, 1.0 / 64)
+        try:
+            cpu_all = oracle_all_cores(args.workload, work, workers)
+        except Exception as e:  # noqa: BLE001 -- a baseline must not cost the GPU measurement
+            cpu_all = {"unavailable": f"{type(e).__name__}: {e}"}
         cpu_combined = combined_baseline(work)
+        if not args.no_parity:
+            try:
+                parity = check_full_products(args.workload, [(p["name"], p["C_host"][0], p["C_host"][1],
+                                                              p["C_host"][2]) for p in prods], workers)
+            except Exception as e:  # noqa: BLE001
+                parity = {"unavailable": f"{type(e).__name__}: {e}"}
 
     extras = {}
     if not args.no_extras and args.workload == "plain":
         extras["batched"] = run_batched(args, dev, binding, torch)
         extras["backward"] = run_backward(args, dev, binding, torch)
+        extras["long_rows"] = run_long_rows(args, dev, binding, torch)
 
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -457,7 +610,8 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD if args.workload == "plain" else args.workload, "indices": "int32", "values": "float64",
                        "l2": "inputs (~2.5 GB per step) larger than L2; no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_combined": cpu_combined, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
+            "cpu_baseline_combined": cpu_combined, "parity_full_size": parity, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(), "detail": detail,
             "three_call": {"ms_per_step": ms_3call, "value": world * flop_step / (ms_3call * 1e-3) / 1e9,
@@ -602,6 +756,108 @@ def run_batched(args, dev, binding, torch):
     out["per_matrix_ms"] = pms
     out["per_matrix_gflops"] = 2 * pm.F / (pms * 1e-3) / 1e9
     out["speedup_batched_vs_per_matrix"] = pms / min(ms, tms)
+    del pm
+    # (ii) the per-matrix loop without host synchronisation: every problem planned once (untimed),
+    # its C sized by its multiplication count, then one spgemm_compute_async per problem
+    items = []
+    try:
+        for dAp, dBp in devp:
+            ws = torch.empty(binding.spgemm_workspace_size(dAp, dBp, topt), dtype=torch.uint8, device=dev)
+            plan = binding.spgemm_plan(dAp, dBp, ws, topt)
+            f = max(binding.spgemm_plan_info(plan)["products"], 1)
+            items.append((plan, dAp, dBp, ws, torch.empty(dAp.rows + 1, dtype=torch.int32, device=dev),
+                          torch.empty(f, dtype=torch.int32, device=dev), torch.empty(f, dtype=torch.float64, device=dev)))
+
+        def loop():
+            for plan, dAp, dBp, _, C_rp, C_col, C_val in items:
+                binding.spgemm_compute_async(plan, dAp.val, dBp.val, C_rp, C_col, C_val)
+
+        loop()
+        torch.cuda.synchronize()
+        for it in items:
+            binding.spgemm_status(it[0])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            loop()
+        e1.record()
+        torch.cuda.synchronize()
+        ams = e0.elapsed_time(e1) / reps
+    finally:
+        for it in items:
+            binding.spgemm_free(it[0])
+    out["per_matrix_async_ms"] = ams
+    out["per_matrix_async_gflops"] = 2 * F / (ams * 1e-3) / 1e9
+    out["per_matrix_async_note"] = "planned beforehand (untimed); one spgemm_compute_async per problem, no host syncs"
+    out["speedup_batched_vs_per_matrix_async"] = ams / min(ms, tms)
+    return out
+
+
+def run_long_rows(args, dev, binding, torch):
+    """The paper's 0.1 % fill workload (Section IV-B): random N x N with round(0.001 N) entries per
+    row, so a row of C gathers about (0.001 N)^2 products.  Per N: plan + single-pass compute under
+    the default classes and under each class forced (warp W, block B, dense G, where the rows fit
+    it), and, for the warp class, its orderings forced (bit vector over [min, max] = the MinMax
+    store, register sort = the Sort store, hash).  GFLOP/s and fraction of the HBM roofline."""
+    bw, _ = hbm_peak()
+    steps = max(3, min(args.steps, 10))
+    off = dict(m1_max_u=-1, m2_max_u=-1)
+    variants = [("default", {}), ("W", off), ("B", dict(off, warp_max_u=-1)),
+                ("G", dict(off, warp_max_u=-1, block_max_u=-1)),
+                ("W-minmax", dict(off, warp_order=1)), ("W-sort", dict(off, warp_order=2)),
+                ("W-hash", dict(off, warp_order=3))]
+    out = {"fill": 0.001, "points": []}
+    for N in (5000, 10000, 20000, 30000, 38000, 50000, 70000):
+        A = synth.random_fill(N, 0.001, synth.SEED_A + N)
+        B = synth.random_fill(N, 0.001, synth.SEED_B + N)
+        dA, dB = binding.DeviceCSR.from_host(A, dev), binding.DeviceCSR.from_host(B, dev)
+        k = int(A.row_ptr[1])
+        pt = {"N": N, "k": k, "products_per_row": k * k, "by_class": {}}
+        for name, o in variants:
+            if name.startswith("W") and k * k > 1024:
+                continue
+            if name == "B" and k * k > 4096:
+                continue
+            opt = binding.options(**o) if o else None
+            ws = torch.empty(binding.spgemm_workspace_size(dA, dB, opt), dtype=torch.uint8, device=dev)
+
+            def step():
+                plan = binding.spgemm_plan(dA, dB, ws, opt)
+                try:
+                    info = binding.spgemm_plan_info(plan)
+                    f = max(info["products"], 1)
+                    C_col = torch.empty(f, dtype=torch.int32, device=dev)
+                    C_val = torch.empty(f, dtype=torch.float64, device=dev)
+                    C_rp = torch.empty(A.rows + 1, dtype=torch.int32, device=dev)
+                    return binding.spgemm_compute(plan, dA.val, dB.val, C_rp, C_col, C_val), info
+                finally:
+                    binding.spgemm_free(plan)
+
+            for _ in range(2):
+                nnz, info = step()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                step()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            t = float(np.median(ts))
+            bmin = roofline.bytes_min(A, B, nnz)
+            pt["by_class"][name] = {"ms": t, "gflops": 2 * info["products"] / (t * 1e-3) / 1e9,
+                                    "frac_hbm": bmin / (t * 1e-3) / 1e9 / bw,
+                                    "rows_per_class": info["rows_per_class"]}
+            pt["nnz_c_per_row"] = nnz / N
+        forced = {c: v["ms"] for c, v in pt["by_class"].items() if c in ("W", "B", "G")}
+        pt["fastest_class"] = min(forced, key=forced.get)
+        orders = {c: v["ms"] for c, v in pt["by_class"].items() if c.startswith("W-")}
+        if orders:
+            pt["fastest_warp_ordering"] = min(orders, key=orders.get)
+        out["points"].append(pt)
+        del dA, dB
+        torch.cuda.empty_cache()
     return out
 
 

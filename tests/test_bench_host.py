@@ -87,3 +87,35 @@ def test_combined_baseline_entry(monkeypatch):
         raise OSError("no C++ compiler")
     monkeypatch.setattr(baseline, "combined", broken)
     assert bench.combined_baseline(work) == {"unavailable": "OSError: no C++ compiler"}
+
+
+def test_oracle_protocol_and_all_cores():
+    import bench
+    work = bench.make_workload("small")
+    line = bench.oracle_protocol(work, 0.25, min_s=0.2, min_runs=3)
+    assert line["runs"] >= 3 and line["value"] >= line["median"] > 0
+    assert line["cores"] == line["threads"] == 1 and line["cpu_model"]
+    allc = bench.oracle_all_cores("small", work, workers=2, min_s=0.2, min_runs=2)
+    assert allc["cores"] == 2 and allc["runs"] >= 2 and allc["value"] > 0
+
+
+def test_full_size_check_against_the_oracle():
+    import bench
+    work = bench.make_workload("small")
+    results = []
+    for name, A, B in work:
+        R = oracle.spgemm(A, B)
+        results.append((name, R["row_ptr"], R["col_idx"], R["val"].copy()))
+    out = bench.check_full_products("small", results, workers=2)
+    for name, _, col, _ in results:
+        v = out[name]
+        assert v["pattern_equal"] and v["max_err_over_sum_abs"] == 0 and v["max_plain_rel_err"] == 0
+        assert v["entries"] == col.size
+    # a planted value error shows in both measures; a planted column error in the pattern check
+    name, rp, col, val = results[1]
+    val[123] *= 1 + 1e-9
+    out = bench.check_full_products("small", [(name, rp, col, val)], workers=2)[name]
+    assert out["pattern_equal"] and 1e-10 < out["max_plain_rel_err"] < 1e-8 and out["max_err_over_sum_abs"] > 1e-10
+    col = col.copy()
+    col[5], col[6] = col[6], col[5]
+    assert not bench.check_full_products("small", [(name, rp, col, val)], workers=2)[name]["pattern_equal"]
