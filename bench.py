@@ -816,7 +816,7 @@ def run_long_rows(args, dev, binding, torch):
         for name, o in variants:
             if name.startswith("W") and k * k > 1024:
                 continue
-            if name == "B" and k * k > 4096:
+            if name == "B" and k * k > 8192:
                 continue
             opt = binding.options(**o) if o else None
             ws = torch.empty(binding.spgemm_workspace_size(dA, dB, opt), dtype=torch.uint8, device=dev)

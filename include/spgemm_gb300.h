@@ -111,8 +111,10 @@ typedef struct {
                              below 2^25 for u_r <= 128 down to 2^22 for u_r > 512, and for u_r <= 32
                              below 2^22 only; else a hash table): u_r <= this (max 1024, default
                              1024) */
-  int32_t block_max_u;    /* block-per-row hash class B: u_r <= this (max 4096, default 4096);
-                             longer rows use a dense accumulator in global memory (class G) */
+  int32_t block_max_u;    /* block-per-row class B (the row's columns ordered by a bit vector over
+                             windows of 2^18 columns, one window after another): u_r <= this (max
+                             8192, default 8192); longer rows use a dense accumulator in global
+                             memory (class G) */
   int32_t dense_slabs;    /* CTAs (each owning one dense accumulator of B.cols doubles and flags, 12
                              bytes per column) for class G; default: as many as fit in 128 MB, at
                              least 2 and at most one per SM of the current device */

@@ -50,13 +50,13 @@ Layout layout(const spgemm_csr_t& A, const spgemm_csr_t& B, int nslabs, const bo
 }
 
 Limits limits_from(const spgemm_options_t* o) {
-  Limits l{8, 32, 64, 1024, 4096};
+  Limits l{8, 32, 64, 1024, 0};
   if (o) {
     if (o->merge_max_k > 0) l.merge_k = std::min(o->merge_max_k, 8);
     if (o->m1_max_u > 0) l.m1_u = std::min(o->m1_max_u, 32);
     if (o->m2_max_u > 0) l.m2_u = std::min(o->m2_max_u, 64);
     if (o->warp_max_u > 0) l.warp_u = std::min(o->warp_max_u, 1024);
-    if (o->block_max_u > 0) l.block_u = std::min(o->block_max_u, 4096);
+    if (o->block_max_u > 0) l.block_u = o->block_max_u;   // clamped by block_limit
     if (o->m1_max_u < 0) l.m1_u = -1;     // negative: class disabled (testing hook)
     if (o->m2_max_u < 0) l.m2_u = -1;
     if (o->warp_max_u < 0) l.warp_u = -1;
@@ -73,6 +73,12 @@ WarpOrder wopts_from(const spgemm_options_t* o) {
   if (o && o->warp_bitvec_ratio > 0) w.bitvec_ratio = std::min(o->warp_bitvec_ratio, 128);
   if (o && o->warp_order >= 0 && o->warp_order <= 3) w.order = o->warp_order;
   return w;
+}
+
+// Class B takes up to BB_MAX_U products per row (the sums of its bit-vector windows).
+void block_limit(Limits& l) {
+  if (l.block_u > 0) l.block_u = std::min(l.block_u, BB_MAX_U);
+  else if (l.block_u == 0) l.block_u = BB_MAX_U;
 }
 
 int slabs_from(const spgemm_options_t* o, int ncols) {
@@ -272,6 +278,7 @@ spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spg
   p->A = to_dev(*A);
   p->B = to_dev(*B);
   p->lim = limits_from(opt);
+  block_limit(p->lim);
   p->nslabs = nslabs;
   p->values_mode = (opt && opt->merge_values >= 0 && opt->merge_values <= 2) ? opt->merge_values : 0;
   p->wopt = wopts_from(opt);
@@ -348,7 +355,8 @@ spgemm_status_t spgemm_symbolic(spgemm_plan_t p, int32_t* C_row_ptr, int64_t* nn
     launch_hash_symbolic(CLS_W, p->A, p->B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s, p->h.max_u_w,
                            p->wopt);
   if (cnt[CLS_B] > 0)
-    launch_hash_symbolic(CLS_B, p->A, p->B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s);
+    launch_hash_symbolic(CLS_B, p->A, p->B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s,
+                         p->h.max_u);
   if (cnt[CLS_G] > 0)
     launch_dense_symbolic(p->A, p->B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs,
                           C_row_ptr, p->ctr, s);
@@ -383,7 +391,8 @@ spgemm_status_t spgemm_numeric(spgemm_plan_t p, const double* A_val, const doubl
     launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s, p->h.max_u_w,
                         p->wopt);
   if (cnt[CLS_B] > 0)
-    launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], p->C_rp, C_col, C_val, p->ctr, s);
+    launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], p->C_rp, C_col, C_val, p->ctr, s,
+                        p->h.max_u);
   if (cnt[CLS_G] > 0)
     launch_dense_numeric(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs, p->C_rp,
                          C_col, C_val, p->ctr, s);
@@ -423,7 +432,8 @@ static spgemm_status_t compute_enqueue(spgemm_plan_t p, const double* A_val, con
       launch_hash_symbolic(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, p->ctr, s, p->h.max_u_w,
                            p->wopt);
     if (cnt[CLS_B] > 0)
-      launch_hash_symbolic(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s);
+      launch_hash_symbolic(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s,
+                           p->h.max_u);
     if (cnt[CLS_G] > 0)
       launch_dense_symbolic(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs,
                             C_row_ptr, p->ctr, s);
@@ -434,7 +444,8 @@ static spgemm_status_t compute_enqueue(spgemm_plan_t p, const double* A_val, con
       launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], C_row_ptr, C_col, C_val, p->ctr, s, p->h.max_u_w,
                         p->wopt);
     if (cnt[CLS_B] > 0)
-      launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, C_col, C_val, p->ctr, s);
+      launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, C_col, C_val, p->ctr, s,
+                          p->h.max_u);
     if (cnt[CLS_G] > 0)
       launch_dense_numeric(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs, C_row_ptr,
                            C_col, C_val, p->ctr, s);
@@ -511,7 +522,8 @@ spgemm_status_t spgemm_replay(spgemm_plan_t p, const double* A_val, const double
     launch_hash_numeric(CLS_W, A, B, (const int*)(p->ws + L.list_w), cnt[CLS_W], p->C_rp, C_col, C_val, p->ctr, s, p->h.max_u_w,
                         p->wopt);
   if (cnt[CLS_B] > 0)
-    launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], p->C_rp, C_col, C_val, p->ctr, s);
+    launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], p->C_rp, C_col, C_val, p->ctr, s,
+                        p->h.max_u);
   if (cnt[CLS_G] > 0)
     launch_dense_numeric(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs, p->C_rp,
                          C_col, C_val, p->ctr, s);

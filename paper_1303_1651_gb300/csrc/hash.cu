@@ -18,11 +18,6 @@
 
 namespace spg {
 
-template <int GROUP>
-__device__ __forceinline__ void group_sync() {
-  if constexpr (GROUP == 32) __syncwarp(); else __syncthreads();
-}
-
 // Insert key; returns slot, sets *fresh when this call created the entry.  -1 when the table is full.
 __device__ __forceinline__ int hash_insert(int* keys, int x, unsigned log2t, bool* fresh) {
   const unsigned mask = (1u << log2t) - 1u;
@@ -40,154 +35,6 @@ __device__ __forceinline__ int hash_insert(int* keys, int x, unsigned log2t, boo
   }
   *fresh = false;
   return -1;
-}
-
-template <int GROUP>
-__device__ __forceinline__ int group_sum(int v, int* s_red) {
-  if constexpr (GROUP == 32) {
-    return __reduce_add_sync(FULL, v);
-  } else {
-    v = __reduce_add_sync(FULL, v);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) s_red[w] = v;
-    __syncthreads();
-    int t = 0;
-    for (int i = 0; i < GROUP / 32; ++i) t += s_red[i];
-    __syncthreads();
-    return t;
-  }
-}
-
-template <int GROUP, int LOG2T, int GPB>
-struct HashSmem {
-  static constexpr int T = 1 << LOG2T;
-  static constexpr size_t sym_per_group = 4 * T;
-  // numeric: vals[T] + cvals[T/2] (doubles), keys[T] + ckeys[T/2] (ints), counter
-  static constexpr size_t num_per_group = 8 * T + 8 * (T / 2) + 4 * T + 4 * (T / 2) + 16;
-  static constexpr size_t sym_bytes = GPB * sym_per_group + 4 * 32;
-  static constexpr size_t num_bytes = GPB * num_per_group + 4 * 32 + 16;
-};
-
-template <int GROUP, int LOG2T, int GPB>
-__global__ void __launch_bounds__(GROUP * GPB)
-k_hash_sym(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __restrict__ counts,
-           Counters* __restrict__ ctr) {
-  using L = HashSmem<GROUP, LOG2T, GPB>;
-  constexpr int T = L::T;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int g = threadIdx.x / GROUP, gt = threadIdx.x % GROUP;
-  int* keys = reinterpret_cast<int*>(smem + g * L::sym_per_group);
-  int* s_red = reinterpret_cast<int*>(smem + GPB * L::sym_per_group);
-  for (int idx = blockIdx.x * GPB + g; idx < count; idx += gridDim.x * GPB) {
-    const int r = list[idx];
-    const int a0 = A.rp[r], a1 = A.rp[r + 1];
-    // table of pow2 >= 2u slots (at most T)
-    int uu = 0;
-    for (int p = a0 + gt; p < a1; p += GROUP) { const int j = __ldg(A.col + p); uu += __ldg(B.rp + j + 1) - __ldg(B.rp + j); }
-    const int u = group_sum<GROUP>(uu, s_red);
-    unsigned lg = 6;
-    while ((1 << lg) < 2 * u && (1 << lg) < T) ++lg;
-    const int TR = 1 << lg;
-    for (int i = gt; i < TR; i += GROUP) keys[i] = KEY_NONE;
-    group_sync<GROUP>();
-    int cnt = 0;
-    bool full = false;
-    for (int p = a0; p < a1; ++p) {
-      const int j = __ldg(A.col + p);
-      const int bs = __ldg(B.rp + j), be = __ldg(B.rp + j + 1);
-      for (int q = bs + gt; q < be; q += GROUP) {
-        bool fresh;
-        const int slot = hash_insert(keys, __ldg(B.col + q), lg, &fresh);
-        if (slot < 0) full = true;
-        cnt += fresh;
-      }
-    }
-    if (full) atomicOr(&ctr->status, ST_TABLE_FULL);
-    const int total = group_sum<GROUP>(cnt, s_red);
-    if (gt == 0) counts[r] = total;
-    group_sync<GROUP>();
-  }
-}
-
-template <int GROUP, int LOG2T, int GPB>
-__global__ void __launch_bounds__(GROUP * GPB)
-k_hash_num(DevCsr A, DevCsr B, const int* __restrict__ list, int count, const int* __restrict__ rp,
-           int* __restrict__ C_col, double* __restrict__ C_val, Counters* __restrict__ ctr) {
-  using L = HashSmem<GROUP, LOG2T, GPB>;
-  constexpr int T = L::T;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int g = threadIdx.x / GROUP, gt = threadIdx.x % GROUP;
-  unsigned char* gb = smem + g * L::num_per_group;
-  double* vals = reinterpret_cast<double*>(gb);
-  double* cvals = vals + T;
-  int* keys = reinterpret_cast<int*>(cvals + T / 2);
-  int* ckeys = keys + T;
-  int* s_n = ckeys + T / 2;
-  int* s_red = reinterpret_cast<int*>(smem + GPB * L::num_per_group);
-  for (int idx = blockIdx.x * GPB + g; idx < count; idx += gridDim.x * GPB) {
-    const int r = list[idx];
-    const int a0 = A.rp[r], a1 = A.rp[r + 1];
-    int uu = 0;
-    for (int p = a0 + gt; p < a1; p += GROUP) { const int j = __ldg(A.col + p); uu += __ldg(B.rp + j + 1) - __ldg(B.rp + j); }
-    const int u = group_sum<GROUP>(uu, s_red);
-    unsigned lg = 6;
-    while ((1 << lg) < 2 * u && (1 << lg) < T) ++lg;
-    const int TR = 1 << lg;
-    for (int i = gt; i < TR; i += GROUP) { keys[i] = KEY_NONE; vals[i] = 0.0; }
-    if (gt == 0) *s_n = 0;
-    group_sync<GROUP>();
-    bool full = false;
-    for (int p = a0; p < a1; ++p) {
-      const int j = __ldg(A.col + p);
-      const double a = __ldg(A.val + p);
-      const int bs = __ldg(B.rp + j), be = __ldg(B.rp + j + 1);
-      for (int q = bs + gt; q < be; q += GROUP) {
-        bool fresh;
-        const int slot = hash_insert(keys, __ldg(B.col + q), lg, &fresh);
-        if (slot < 0) { full = true; continue; }
-        atomicAdd(&vals[slot], __dmul_rn(a, __ldg(B.val + q)));
-      }
-    }
-    if (full) atomicOr(&ctr->status, ST_TABLE_FULL);
-    group_sync<GROUP>();
-    // compact the touched slots (any order), then sort them by column
-    for (int i = gt; i < TR; i += GROUP) {
-      const int k = keys[i];
-      if (k != KEY_NONE) {
-        const int pos = atomicAdd(s_n, 1);
-        if (pos < T / 2) { ckeys[pos] = k; cvals[pos] = vals[i]; }
-      }
-    }
-    group_sync<GROUP>();
-    const int n = min(*s_n, T / 2);
-    int n2 = 1;
-    while (n2 < n) n2 <<= 1;
-    for (int i = n + gt; i < n2; i += GROUP) { ckeys[i] = KEY_NONE; cvals[i] = 0.0; }
-    group_sync<GROUP>();
-    for (int kk = 2; kk <= n2; kk <<= 1) {
-      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        for (int i = gt; i < n2; i += GROUP) {
-          const int ixj = i ^ jj;
-          if (ixj > i) {
-            const int ki = ckeys[i], kj = ckeys[ixj];
-            const bool up = (i & kk) == 0;
-            if ((ki > kj) == up) {
-              ckeys[i] = kj; ckeys[ixj] = ki;
-              const double t = cvals[i]; cvals[i] = cvals[ixj]; cvals[ixj] = t;
-            }
-          }
-        }
-        group_sync<GROUP>();
-      }
-    }
-    const int g0 = rp[r], g1 = rp[r + 1];
-    if (gt == 0 && g1 - g0 != n) atomicOr(&ctr->status, ST_MISMATCH);
-    for (int i = gt; i < n && g0 + i < g1; i += GROUP) {
-      C_col[g0 + i] = ckeys[i];
-      C_val[g0 + i] = cvals[i];
-    }
-    group_sync<GROUP>();
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -557,6 +404,202 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
   }
 }
 
+// ---------------------------------------------------------------------------
+// Class B: one block of 512 threads per row, its columns ordered by a bit vector -- the MinMax
+// store of Section IV-B with the flags as bits, kept in shared memory; no hash table, no sort.
+// The bit vector covers a window of BB_WINDOW columns above the row's smallest column not yet
+// done; a row whose columns span more is done window by window, each window starting at the
+// smallest column past the last.  Per window:
+//   1. mark  -- each product in the window sets its column's bit (a warp per entry of A, lanes
+//               along the row of B); the window's largest column and the next window's first
+//               column come out of the same pass;
+//   2. rank  -- the words up to the largest are ranked by a block prefix of their popcounts,
+//               512 words per round;
+//   3. sum   -- numeric: every product a_rj * b_jx in the window is added to sums[rank of its
+//               column] (products rounded on their own, added in no fixed order);
+//   4. write -- the set bits, walked in order, give the window's entries of C, columns ascending,
+//               after the entries of the windows before it.
+// Sums hold up to BB_MAX_U entries per window; class B rows have at most that many products.  When
+// B has at most BB_WINDOW columns the window starts at column 0 and the first pass (the row's
+// smallest column) is skipped.
+// ---------------------------------------------------------------------------
+constexpr int BB_THREADS = 512;
+constexpr int BB_WARPS = BB_THREADS / 32;
+constexpr int BB_WINDOW = 1 << 18;   // columns covered by one bit vector (bb_words)
+
+// words of the bit vector: one window, or all of B's columns when they are fewer
+__host__ __device__ inline int bb_words(int ncols) {
+  const int n = ncols < 1 ? 1 : ncols;
+  return ((n < (1 << 18) ? n : (1 << 18)) + 31) / 32;
+}
+
+size_t block_bitvec_smem(int ncols, int sums, bool num) {
+  const size_t words = (size_t)bb_words(ncols);
+  return (num ? 8 * (size_t)sums : 0) + 4 * words + (2 * words + 15) / 16 * 16 + 4 * 4 * BB_WARPS;
+}
+
+// Block minimum and maximum (reduction slots red[0 .. 2 * BB_WARPS)).
+__device__ __forceinline__ void bb_minmax(int& mn, int& mx, int* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  mn = __reduce_min_sync(FULL, mn);
+  mx = __reduce_max_sync(FULL, mx);
+  if (lane == 0) { red[warp] = mn; red[BB_WARPS + warp] = mx; }
+  __syncthreads();
+  mn = INT_MAX; mx = INT_MIN;
+#pragma unroll
+  for (int i = 0; i < BB_WARPS; ++i) { mn = min(mn, red[i]); mx = max(mx, red[BB_WARPS + i]); }
+  __syncthreads();   // red is reused
+}
+
+template <bool NUM>
+__global__ void __launch_bounds__(BB_THREADS)
+k_block_bitvec(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int sums_cap, int* __restrict__ rp,
+               int* __restrict__ C_col, double* __restrict__ C_val, Counters* __restrict__ ctr) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = bb_words(B.cols);
+  double* sums = reinterpret_cast<double*>(smem);                                          // [sums_cap] (NUM)
+  unsigned* bits = reinterpret_cast<unsigned*>(smem + (NUM ? 8 * (size_t)sums_cap : 0));   // [W]
+  unsigned short* rank = reinterpret_cast<unsigned short*>(bits + W);                      // [W]
+  int* red = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(rank) + ((size_t)2 * W + 15) / 16 * 16);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool one_window = B.cols <= BB_WINDOW;
+  for (int w = tid; w < W; w += BB_THREADS) bits[w] = 0u;
+  __syncthreads();
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int r = list[idx];
+    const int a0 = __ldg(A.rp + r), a1 = __ldg(A.rp + r + 1);
+    int g0 = 0, g1 = 0;
+    if (NUM) { g0 = __ldg(rp + r); g1 = __ldg(rp + r + 1); }
+    // the first window's start: column 0, or the row's smallest column
+    int lo = 0;
+    bool bad = false;
+    if (!one_window) {
+      int mn = INT_MAX, mx = INT_MIN;
+      for (int e = a0 + warp; e < a1; e += BB_WARPS) {
+        const int j = __ldg(A.col + e);
+        const int bs = __ldg(B.rp + j), be = __ldg(B.rp + j + 1);
+        for (int q = bs + lane; q < be; q += 32) mn = min(mn, __ldg(B.col + q));
+      }
+      bb_minmax(mn, mx, red);
+      lo = mn;
+    }
+    int done = 0;   // entries of the row in the windows before this one
+    while (lo != INT_MAX) {   // block-uniform
+      const long long hi = (long long)lo + BB_WINDOW;   // window [lo, hi)
+      // 1. mark
+      int wmax = INT_MIN, next = INT_MAX;
+      for (int e = a0 + warp; e < a1; e += BB_WARPS) {
+        const int j = __ldg(A.col + e);
+        const int bs = __ldg(B.rp + j), be = __ldg(B.rp + j + 1);
+        for (int q = bs + lane; q < be; q += 32) {
+          const int c = __ldg(B.col + q);
+          if ((unsigned)c >= (unsigned)B.cols) { bad = true; continue; }
+          if (c < lo) continue;
+          if (c >= hi) { next = min(next, c); continue; }
+          const int d = c - lo;
+          atomicOr(&bits[d >> 5], 1u << (d & 31));
+          wmax = max(wmax, d);
+        }
+      }
+      {
+        int nmin = next, wmx = wmax;
+        bb_minmax(nmin, wmx, red);   // red[0..]: next window (min), this window's largest (max)
+        next = nmin;
+        wmax = wmx;
+      }
+      const int whi = wmax >= 0 ? wmax >> 5 : -1;
+      // 2. rank the words 0 .. whi
+      int total = 0;
+      for (int wb = 0; wb <= whi; wb += BB_THREADS) {
+        const int w = wb + tid;
+        const int pc = w <= whi ? __popc(bits[w]) : 0;
+        int incl = pc;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(FULL, incl, d);
+          if (lane >= d) incl += y;
+        }
+        if (lane == 31) red[2 * BB_WARPS + warp] = incl;
+        __syncthreads();
+        int woff = 0, round = 0;
+#pragma unroll
+        for (int i = 0; i < BB_WARPS; ++i) {
+          const int t = red[2 * BB_WARPS + i];
+          woff += i < warp ? t : 0;
+          round += t;
+        }
+        if (NUM && w <= whi) rank[w] = (unsigned short)(total + woff + incl - pc);
+        total += round;
+        __syncthreads();   // red is rewritten by the next round
+      }
+      if (NUM) {
+        if (total > sums_cap) {
+          if (tid == 0) atomicOr(&ctr->status, ST_TABLE_FULL);   // the launch sizes sums for every row
+        } else {
+          // 3. sums
+          for (int i = tid; i < total; i += BB_THREADS) sums[i] = 0.0;
+          __syncthreads();
+          for (int e = a0 + warp; e < a1; e += BB_WARPS) {
+            const int j = __ldg(A.col + e);
+            const double a = __ldg(A.val + e);
+            const int bs = __ldg(B.rp + j), be = __ldg(B.rp + j + 1);
+            for (int q = bs + lane; q < be; q += 32) {
+              const int c = __ldg(B.col + q);
+              if ((unsigned)c >= (unsigned)B.cols || c < lo || c >= hi) continue;
+              const int d = c - lo;
+              const int w = d >> 5;
+              const int k = rank[w] + __popc(bits[w] & ((1u << (d & 31)) - 1u));
+              atomicAdd(&sums[k], __dmul_rn(a, __ldg(B.val + q)));
+            }
+          }
+          __syncthreads();
+          // 4. write, consecutive threads on consecutive words
+          for (int w = tid; w <= whi; w += BB_THREADS) {
+            unsigned b = bits[w];
+            int k = rank[w];
+            while (b) {
+              const int bit = __ffs(b) - 1;
+              b &= b - 1;
+              const int o = done + k;
+              if (o < g1 - g0) {
+                C_col[g0 + o] = lo + (w << 5) + bit;
+                C_val[g0 + o] = sums[k];
+              }
+              ++k;
+            }
+          }
+        }
+      }
+      done += total;
+      __syncthreads();
+      for (int w = tid; w <= whi; w += BB_THREADS) bits[w] = 0u;
+      __syncthreads();
+      lo = next;
+    }
+    if (bad) atomicOr(&ctr->status, ST_INVALID);
+    if (tid == 0) {
+      if (!NUM) rp[r] = done;
+      else if (g1 - g0 != done) atomicOr(&ctr->status, ST_MISMATCH);
+    }
+  }
+}
+
+int block_bitvec_window() { return BB_WINDOW; }
+
+template <bool NUM>
+static void launch_block_bitvec(const DevCsr& A, const DevCsr& B, const int* list, int count, int umax, int* rp,
+                                int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
+  if (count <= 0) return;
+  const int sums_cap = std::max(1, std::min(umax, BB_MAX_U));
+  const size_t bytes = block_bitvec_smem(B.cols, sums_cap, NUM);
+  auto kern = k_block_bitvec<NUM>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BB_THREADS, bytes);
+  const int blocks = std::max(1, std::min(count, num_sms() * std::max(per_sm, 1)));
+  kern<<<blocks, BB_THREADS, bytes, s>>>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr);
+}
+
 template <bool NUM, int U>
 static void launch_warp_row_u(const DevCsr& A, const DevCsr& B, const int* list, int count, int* rp, int* C_col,
                               double* C_val, Counters* ctr, cudaStream_t s, WarpOrder wo) {
@@ -580,38 +623,16 @@ static void launch_warp_row(const DevCsr& A, const DevCsr& B, const int* list, i
   else launch_warp_row_u<NUM, WR_UMAX>(A, B, list, count, rp, C_col, C_val, ctr, s, wo);
 }
 
-template <int GROUP, int LOG2T, int GPB, bool NUM>
-static void launch_hash(const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts, const int* rp,
-                        int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
-  if (count <= 0) return;
-  using L = HashSmem<GROUP, LOG2T, GPB>;
-  const size_t bytes = NUM ? L::num_bytes : L::sym_bytes;
-  int per_sm = 0;
-  if (NUM) {
-    auto kern = k_hash_num<GROUP, LOG2T, GPB>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GROUP * GPB, bytes);
-    const int blocks = std::max(1, std::min((count + GPB - 1) / GPB, num_sms() * std::max(per_sm, 1)));
-    kern<<<blocks, GROUP * GPB, bytes, s>>>(A, B, list, count, rp, C_col, C_val, ctr);
-  } else {
-    auto kern = k_hash_sym<GROUP, LOG2T, GPB>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GROUP * GPB, bytes);
-    const int blocks = std::max(1, std::min((count + GPB - 1) / GPB, num_sms() * std::max(per_sm, 1)));
-    kern<<<blocks, GROUP * GPB, bytes, s>>>(A, B, list, count, counts, ctr);
-  }
-}
-
 void launch_hash_symbolic(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts,
                           Counters* ctr, cudaStream_t s, int umax, WarpOrder wo) {
   if (cls == CLS_W) launch_warp_row<false>(A, B, list, count, umax, counts, nullptr, nullptr, ctr, s, wo);
-  else launch_hash<512, 13, 1, false>(A, B, list, count, counts, nullptr, nullptr, nullptr, ctr, s);
+  else launch_block_bitvec<false>(A, B, list, count, umax, counts, nullptr, nullptr, ctr, s);
 }
 
 void launch_hash_numeric(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, const int* rp,
                          int* C_col, double* C_val, Counters* ctr, cudaStream_t s, int umax, WarpOrder wo) {
   if (cls == CLS_W) launch_warp_row<true>(A, B, list, count, umax, const_cast<int*>(rp), C_col, C_val, ctr, s, wo);
-  else launch_hash<512, 13, 1, true>(A, B, list, count, nullptr, rp, C_col, C_val, ctr, s);
+  else launch_block_bitvec<true>(A, B, list, count, umax, const_cast<int*>(rp), C_col, C_val, ctr, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -42,8 +42,12 @@ struct WarpOrder {
   int order = 0;
 };
 
-// a2/a4, hash classes W (warp per row) and B (block per row), rows from a list.  umax: the longest
-// W row's products (sizes the W kernel's shared memory); unused for class B.
+// a2/a4, classes W (warp per row) and B (block per row), rows from a list.  umax: the longest row
+// of the class (W: sizes the W kernel's shared memory; B: the sums of its bit-vector windows, at
+// most BB_MAX_U).  Class B orders each row by a bit vector over windows of block_bitvec_window()
+// columns.
+constexpr int BB_MAX_U = 8192;
+int block_bitvec_window();
 void launch_hash_symbolic(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts,
                           Counters* ctr, cudaStream_t s, int umax = 1024, WarpOrder wo = WarpOrder());
 void launch_hash_numeric(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, const int* rp,

@@ -553,8 +553,10 @@ struct PairSmem {
   static constexpr bool V = MODE != MODE_SYM;
   static constexpr size_t s_val = 0;                               // double [SLOTS]  b_jx, later group sums
   static constexpr size_t s_col = s_val + (V ? 8 * SLOTS : 0);     // uint   [SLOTS]  columns, later output keys
-  static constexpr size_t r_run = s_col + 4 * SLOTS;               // int2   [ROWS * 8]; s_a (double [8][ROWS]) later
-  static constexpr size_t s_cfr = r_run + 8 * ROWS * MERGE_K;      // int    [32]  run holding product 32c
+  static constexpr size_t r_run = s_col + 4 * SLOTS;               // int2   [ROWS * 8]; s_a later: a_rj of row t,
+                                                                   // run q at [t * 9 + q] (an odd stride puts the
+                                                                   // two lanes of a row on different banks)
+  static constexpr size_t s_cfr = r_run + 8 * ROWS * (MERGE_K + 1);   // int  [32]  run holding product 32c
   static constexpr size_t bytes = s_cfr + 4 * 32;
 };
 
@@ -681,7 +683,7 @@ __device__ __forceinline__ void merge_tile_pair(const MergeArgs& g, int tile, un
 #pragma unroll
       for (int i = 0; i < MERGE_K; ++i) {
         if ((nem >> i) & 1u) {
-          s_a[q * L::ROWS + t] = av[i];
+          s_a[t * (MERGE_K + 1) + q] = av[i];
           ++q;
         }
       }
@@ -751,7 +753,7 @@ __device__ __forceinline__ void merge_tile_pair(const MergeArgs& g, int tile, un
         double a = 0.0, b = 0.0;
         if (valid) {
           b = s_val[base + idx];
-          a = s_a[run * L::ROWS + t];
+          a = s_a[t * (MERGE_K + 1) + run];
         }
         const bool same = j > 0 && ((samemask >> j) & 1u);
         acc = __fma_rn(a, b, same ? acc : 0.0);
@@ -780,7 +782,7 @@ __device__ __forceinline__ void merge_tile_pair(const MergeArgs& g, int tile, un
           const unsigned kj = key[j];
           const int idx = (int)(kj & 63u);
           const int run = run_rank(starts, idx);
-          acc2 = __fma_rn(s_a[run * L::ROWS + t], s_val[base + idx], acc2);
+          acc2 = __fma_rn(s_a[t * (MERGE_K + 1) + run], s_val[base + idx], acc2);
           if (j == glen - 1) {
             s_col[base + ends_lo] = kj;
             s_val[base + idx] = acc2;

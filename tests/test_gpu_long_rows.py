@@ -1,8 +1,8 @@
 """Rows of many products on the GPU, against the CPU oracle.
 
 * The 0.1 % fill workload of Section IV-B (random N x N matrices with round(0.001 N) entries per
-  row): at N = 38000 every row of C gathers 38^2 = 1444 products (the block-hash class B); at
-  N = 70000, 4900 (the dense class G).  C is checked whole on the device (row pointer, strictly
+  row): at N = 38000 every row of C gathers 38^2 = 1444 products, at N = 70000 4900: the block
+  class B (its bit-vector form, B having at most 2^18 columns), and the dense class G when forced.  C is checked whole on the device (row pointer, strictly
   ascending columns in range) and 512 rows are compared with the oracle's product of those rows.
 * The class-W orderings (the per-row "Combined" switch of Section IV-B): every forced ordering
   and the bit-vector threshold, on rows whose column ranges reach each ordering.
@@ -39,8 +39,9 @@ def device_product(A, B, opt=None):
     return C_rp, C_col[:nnz], C_val[:nnz], nnz, info
 
 
-@pytest.mark.parametrize("N,forced,cls", [(38_000, None, "B"), (38_000, "G", "G"), (70_000, None, "G")],
-                         ids=["38000-block", "38000-dense", "70000-dense"])
+@pytest.mark.parametrize("N,forced,cls", [(38_000, None, "B"), (38_000, "G", "G"), (70_000, None, "B"),
+                                         (70_000, "G", "G")],
+                         ids=["38000-block", "38000-dense", "70000-block", "70000-dense"])
 def test_fill_one_per_mille(N, forced, cls):
     A = synth.random_fill(N, 0.001, synth.SEED_A + N)
     B = synth.random_fill(N, 0.001, synth.SEED_B + N)
@@ -55,12 +56,28 @@ def test_fill_one_per_mille(N, forced, cls):
 
 @PATHS
 def test_many_dense_rows(fused):
-    # about 700 rows of more than 4096 products: class G, spread over the default number of slabs
+    # about 700 rows of more than 4096 products: class G (the block class capped at 4096),
+    # spread over the default number of slabs
     A = synth.random_lengths(np.full(700, 90), 3000, 461)
     B = synth.random_k(3000, 60, 462, ncols=20000)
-    C = gpu_product(A, B, fused=fused)
+    C = gpu_product(A, B, binding.options(block_max_u=4096), fused=fused)
     assert C["info"]["rows_per_class"]["G"] > 600, C["info"]["rows_per_class"]
     compare(C, oracle.spgemm(A, B))
+
+
+@PATHS
+@pytest.mark.parametrize("ncols,k,kb", [(20_000, 90, 60), (262_144, 60, 40), (262_145, 60, 40), (3_000_000, 45, 45),
+                                        (1_000_000, 90, 80)],
+                         ids=["one-window-5000", "one-window-limit", "two-windows", "many-windows",
+                              "many-windows-7000"])
+def test_block_class_windows(ncols, k, kb, fused):
+    # class B orders a row by a bit vector over windows of 2^18 columns: one window when B has at
+    # most 2^18 columns, else as many as the row's columns span (rows up to 8192 products)
+    A = synth.random_lengths(np.full(500, k), 3000, 463)
+    B = synth.random_k(3000, kb, 464, ncols=ncols)
+    C = gpu_product(A, B, fused=fused)
+    assert C["info"]["rows_per_class"]["B"] > 400, C["info"]["rows_per_class"]
+    compare(C, oracle.spgemm(A, B), single=True)
 
 
 ORDERINGS = [dict(warp_order=1), dict(warp_order=2), dict(warp_order=3), dict(warp_bitvec_ratio=2),
