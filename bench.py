@@ -971,8 +971,28 @@ def run_sweep(args):
                 step_ms.append(e0.elapsed_time(e1))
                 kern_ms.append(ev[2 * i + 1][0].elapsed_time(ev[2 * i + 1][1]))
             assert nnz == pt["nnz_c"]
+            # the same product through spgemm_multiply: one call, one read-back, C preallocated with
+            # capacity F (a caller that reuses its buffers)
+            cap = max(pt["F"], 1)
+            oC_col = torch.empty(cap, dtype=torch.int32, device=dev)
+            oC_val = torch.empty(cap, dtype=torch.float64, device=dev)
+            for _ in range(W):
+                binding.spgemm_multiply(dA, dB, C_rp, oC_col, oC_val, ws, None, stream)
+            one_ms = []
+            for i in range(K):
+                flush.zero_()
+                e0, e1 = ev[2 * i]
+                e0.record(stream)
+                onnz, _ = binding.spgemm_multiply(dA, dB, C_rp, oC_col, oC_val, ws, None, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                one_ms.append(e0.elapsed_time(e1))
+            assert onnz == pt["nnz_c"]
+            del oC_col, oC_val
             bmin = roofline.bytes_min(A, B, nnz)
             ms, kms = float(np.median(step_ms)), float(np.median(kern_ms))
+            oms = float(np.median(one_ms))
+            pt.update({"one_sync_ms": oms, "one_sync_gflops": 2 * pt["F"] / (oms * 1e-3) / 1e9})
             pt.update({"ms": ms, "gflops": 2 * pt["F"] / (ms * 1e-3) / 1e9, "bytes_min": bmin,
                        "frac": bmin / (ms * 1e-3) / 1e9 / bw, "kernel_ms": kms,
                        "kernel_gflops": 2 * pt["F"] / (kms * 1e-3) / 1e9,
@@ -989,6 +1009,8 @@ def run_sweep(args):
                                    "grid and random*random with 4, 8, 16 distinct columns per row",
                        "l2": "512 MB buffer written before every timed step",
                        "step": "plan (binning, F read back) + single-pass compute (nnz(C) read back)",
+                       "one_sync": "spgemm_multiply: binning and single-pass compute in one call, one read-back, "
+                                   "C preallocated with capacity F",
                        "kernel": "the compute call's kernels alone (events around them)"},
             "peak": {"hbm_gbs": bw, "kind": f"{bw_kind} (MEASURED_PEAKS.json hbm_gbs)"},
             "clocks": clk.summary(), "points": points}

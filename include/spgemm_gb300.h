@@ -235,6 +235,26 @@ spgemm_status_t spgemm_compute_async(spgemm_plan_t plan, const double* A_val, co
                                      int32_t* C_row_ptr, int32_t* C_col, double* C_val, int64_t capacity,
                                      int64_t* nnz_c_device, void* stream);
 
+/* The whole product in one call with one host synchronisation: spgemm_plan + spgemm_compute without
+ * the read-back between them, for small products, where that read-back and the launches cost more
+ * than the kernels.  As in Section IV-B, C is stored row by row into one block sized by the caller;
+ * the call returns the multiplication count F (Section III), which always suffices as capacity.
+ *   A, B         -- device descriptors WITH values (and the storage options of spgemm_plan).
+ *   opt          -- may be NULL.
+ *   workspace    -- as for spgemm_plan (spgemm_workspace_size bytes, 256-byte aligned).
+ *   C_row_ptr    -- device, A.rows + 1 int32.
+ *   C_col, C_val -- device, `capacity` entries each.
+ *   nnz_c        -- host, receives nnz(C) (also on OVERFLOW).
+ *   products     -- host, receives F (also on OVERFLOW): retry with capacity >= F.
+ * No plan is kept.  The class kernels are launched before the row classes are known (each reads
+ * its row count on the device), so a product whose rows all fall in one class still pays a few
+ * empty launches.  Enqueues on stream and synchronises it once.  Errors: INVALID, ALLOC, OVERFLOW
+ * (nnz(C) > capacity or > INT32_MAX; nothing is written past `capacity` entries), TABLE_FULL,
+ * TIMEOUT, CUDA. */
+spgemm_status_t spgemm_multiply(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
+                                void* workspace, size_t workspace_bytes, int32_t* C_row_ptr, int32_t* C_col,
+                                double* C_val, int64_t capacity, int64_t* nnz_c, int64_t* products, void* stream);
+
 /* Pattern reuse: new values of A and B, the same structures, C's structure kept.
  *
  * The row-major loop of Section IV-A visits the products of a row in a fixed order (A's entries

@@ -84,6 +84,8 @@ def load():
         lib.spgemm_replay_size.argtypes = [vp, P(ctypes.c_size_t)]
         lib.spgemm_replay_record.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
         lib.spgemm_replay.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.spgemm_multiply.argtypes = [P(spgemm_csr_t), P(spgemm_csr_t), P(spgemm_options_t), vp, ctypes.c_size_t,
+                                        vp, vp, vp, ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_int64), vp]
         lib.spgemm_error_string.argtypes = [ctypes.c_int]
         lib.spgemm_error_string.restype = ctypes.c_char_p
         lib.spgemm_version.restype = ctypes.c_int32
@@ -91,7 +93,7 @@ def load():
                      "spgemm_compute", "spgemm_status", "spgemm_plan_info", "spgemm_free",
                      "spgemm_plan_set_events", "spgemm_compute_async", "spgemm_backward_workspace_size",
                      "spgemm_backward", "spgemm_scan_counts_noalloc", "spgemm_replay_size",
-                     "spgemm_replay_record", "spgemm_replay"):
+                     "spgemm_replay_record", "spgemm_replay", "spgemm_multiply"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -293,6 +295,46 @@ def spgemm_replay(plan: int, A_val: torch.Tensor, B_val: torch.Tensor, map_buf: 
                   C_val: torch.Tensor, stream=None):
     _check(load().spgemm_replay(plan, _ptr(A_val), _ptr(B_val), map_buf.data_ptr(), _ptr(C_col), _ptr(C_val),
                                 _stream(stream)), "spgemm_replay")
+
+
+def spgemm_multiply(A, B, C_row_ptr: torch.Tensor, C_col: torch.Tensor, C_val: torch.Tensor, workspace: torch.Tensor,
+                    opt: spgemm_options_t | None = None, stream=None, raise_on_overflow: bool = True):
+    """Plan + single-pass product in one call (one host synchronisation); C's capacity is
+    min(C_col.numel(), C_val.numel()).  Returns (nnz(C), F).  With raise_on_overflow=False an
+    OVERFLOW (capacity below nnz(C)) returns (nnz(C), F) too, so the caller can resize C to F."""
+    opt = with_storage(A, B, opt)
+    a, b = A.desc(True), B.desc(True)
+    nnz, F = ctypes.c_int64(0), ctypes.c_int64(0)
+    cap = min(C_col.numel(), C_val.numel())
+    code = load().spgemm_multiply(ctypes.byref(a), ctypes.byref(b), ctypes.byref(opt) if opt else None,
+                                  workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                  C_row_ptr.data_ptr(), _ptr(C_col), _ptr(C_val), cap, ctypes.byref(nnz),
+                                  ctypes.byref(F), _stream(stream))
+    if code == 3 and not raise_on_overflow:
+        return int(nnz.value), int(F.value)
+    _check(code, "spgemm_multiply")
+    return int(nnz.value), int(F.value)
+
+
+def multiply_once(A, B, opt: spgemm_options_t | None = None, stream=None, capacity: int | None = None,
+                  workspace: torch.Tensor | None = None) -> DeviceCSR:
+    """C = A*B through spgemm_multiply: one call, one host synchronisation when `capacity` (default
+    nnz(A) + nnz(B) + rows of A) holds C; otherwise a second call with C sized by F."""
+    opt = with_storage(A, B, opt)
+    dev = A.val.device
+    need = spgemm_workspace_size(A, B, opt)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    cap = max(capacity if capacity is not None else A.nnz + B.nnz + A.rows, 1)
+    C_rp = torch.empty(A.rows + 1, dtype=torch.int32, device=dev)
+    C_col = torch.empty(cap, dtype=torch.int32, device=dev)
+    C_val = torch.empty(cap, dtype=torch.float64, device=dev)
+    nnz, F = spgemm_multiply(A, B, C_rp, C_col, C_val, workspace, opt, stream, raise_on_overflow=False)
+    if nnz > cap:
+        C_col = torch.empty(max(F, 1), dtype=torch.int32, device=dev)
+        C_val = torch.empty(max(F, 1), dtype=torch.float64, device=dev)
+        nnz, F = spgemm_multiply(A, B, C_rp, C_col, C_val, workspace, opt, stream)
+    return DeviceCSR(A.rows, B.cols, C_rp, C_col[:nnz], C_val[:nnz])
 
 
 def spgemm_scan_counts_noalloc(row_ptr: torch.Tensor, rows: int | None = None, stream=None) -> int:

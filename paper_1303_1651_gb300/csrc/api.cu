@@ -260,21 +260,24 @@ spgemm_status_t spgemm_workspace_size(const spgemm_csr_t* A, const spgemm_csr_t*
   return SPGEMM_OK;
 }
 
-spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spgemm_csr_t* B,
-                            const spgemm_options_t* opt, void* workspace, size_t workspace_bytes, void* stream) {
-  if (!out) return SPGEMM_ERR_INVALID;
-  *out = nullptr;
+// Checks of spgemm_plan's arguments (host only); on success fills csc, nslabs and the layout.
+static spgemm_status_t plan_args(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
+                                 void* workspace, size_t workspace_bytes, bool csc[2], int* nslabs, Layout* L) {
   if (!storage_ok(opt)) return SPGEMM_ERR_INVALID;
-  const bool csc[2] = {csc_of(opt, 0), csc_of(opt, 1)};
+  csc[0] = csc_of(opt, 0);
+  csc[1] = csc_of(opt, 1);
   if (!desc_ok(A, csc[0]) || !desc_ok(B, csc[1]) || A->cols != B->rows) return SPGEMM_ERR_INVALID;
   if (!workspace || ((uintptr_t)workspace % ALIGN) != 0) return SPGEMM_ERR_INVALID;
-  const int nslabs = slabs_from(opt, B->cols);
-  const Layout L = layout(*A, *B, nslabs, csc);
-  if (workspace_bytes < L.total || fault_is("alloc")) return SPGEMM_ERR_ALLOC;
-  cudaStream_t s = (cudaStream_t)stream;
-  spgemm_plan_s* p = new (std::nothrow) spgemm_plan_s();
-  if (!p) return SPGEMM_ERR_ALLOC;
-  p->pinned = pinned_take();
+  *nslabs = slabs_from(opt, B->cols);
+  *L = layout(*A, *B, *nslabs, csc);
+  if (workspace_bytes < L->total || fault_is("alloc")) return SPGEMM_ERR_ALLOC;
+  return SPGEMM_OK;
+}
+
+// Enqueue the plan's device work (conversion of operands given by columns, optional validation,
+// binning) on s; the counters stay on the device.
+static void plan_enqueue(spgemm_plan_s* p, const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
+                         void* workspace, const bool csc[2], int nslabs, const Layout& L, cudaStream_t s) {
   p->A = to_dev(*A);
   p->B = to_dev(*B);
   p->lim = limits_from(opt);
@@ -319,6 +322,22 @@ spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spg
   int* lists[NUM_CLS] = {nullptr, nullptr, (int*)(p->ws + L.list_w), (int*)(p->ws + L.list_b),
                          (int*)(p->ws + L.list_g)};
   launch_bin(p->A, p->B, p->lim, p->ws + L.cls, lists, p->ctr, s);
+}
+
+spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spgemm_csr_t* B,
+                            const spgemm_options_t* opt, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!out) return SPGEMM_ERR_INVALID;
+  *out = nullptr;
+  bool csc[2];
+  int nslabs = 0;
+  Layout L{};
+  const spgemm_status_t a = plan_args(A, B, opt, workspace, workspace_bytes, csc, &nslabs, &L);
+  if (a != SPGEMM_OK) return a;
+  cudaStream_t s = (cudaStream_t)stream;
+  spgemm_plan_s* p = new (std::nothrow) spgemm_plan_s();
+  if (!p) return SPGEMM_ERR_ALLOC;
+  p->pinned = pinned_take();
+  plan_enqueue(p, A, B, opt, workspace, csc, nslabs, L, s);
   if (read_counters(p, s) != cudaSuccess) {
     delete p;
     return SPGEMM_ERR_CUDA;
@@ -331,6 +350,61 @@ spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spg
   p->state = 1;
   *out = p;
   return SPGEMM_OK;
+}
+
+// spgemm_multiply: binning and the single-pass product enqueued together.  The host does not know
+// the row classes yet, so every class kernel is launched over an upper bound of rows and reads its
+// row count on the device (a class with no rows costs an empty launch), the dense slabs are cleared
+// by their kernel, and both tile forms of the fused pass are launched (the one the binning did not
+// choose returns at once).  The counters are read back once, at the end.
+spgemm_status_t spgemm_multiply(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
+                                void* workspace, size_t workspace_bytes, int32_t* C_row_ptr, int32_t* C_col,
+                                double* C_val, int64_t capacity, int64_t* nnz_c, int64_t* products, void* stream) {
+  if (!nnz_c || !products || !C_row_ptr || capacity < 0) return SPGEMM_ERR_INVALID;
+  if ((!C_col || !C_val) && capacity > 0) return SPGEMM_ERR_INVALID;
+  bool csc[2];
+  int nslabs = 0;
+  Layout L{};
+  const spgemm_status_t a = plan_args(A, B, opt, workspace, workspace_bytes, csc, &nslabs, &L);
+  if (a != SPGEMM_OK) return a;
+  if ((!A->val && A->nnz > 0) || (!B->val && B->nnz > 0)) return SPGEMM_ERR_INVALID;
+  if (fault_is("nnz_overflow")) capacity = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  spgemm_plan_s p;
+  p.pinned = pinned_take();
+  plan_enqueue(&p, A, B, opt, workspace, csc, nslabs, L, s);
+  const int m = p.A.rows;
+  if (m == 0) {
+    cudaMemsetAsync(C_row_ptr, 0, sizeof(int32_t), s);
+  } else {
+    DevCsr Av, Bv;
+    prepare_values(&p, A->val, B->val, Av, Bv, s);
+    cudaMemsetAsync(&p.ctr->ticket, 0, sizeof(unsigned), s);
+    cudaMemsetAsync(p.ws + L.fused, 0, fused_tile_state_bytes(m), s);
+    const int* cnt_dev = p.ctr->count;
+    const int* lw = (const int*)(p.ws + L.list_w);
+    const int* lb = (const int*)(p.ws + L.list_b);
+    const int* lg = (const int*)(p.ws + L.list_g);
+    const Limits& lim = p.lim;
+    if (lim.warp_u > 0)
+      launch_hash_symbolic(CLS_W, Av, Bv, lw, m, C_row_ptr, p.ctr, s, lim.warp_u, p.wopt, cnt_dev + CLS_W);
+    if (lim.block_u > 0) launch_hash_symbolic(CLS_B, Av, Bv, lb, m, C_row_ptr, p.ctr, s, lim.block_u, p.wopt, cnt_dev + CLS_B);
+    launch_dense_symbolic(Av, Bv, lg, m, p.ws + L.slabs, p.nslabs, C_row_ptr, p.ctr, s, cnt_dev + CLS_G, true);
+    for (int wide = 0; wide < 2; ++wide)
+      launch_merge_fused(wide, p.values_mode, Av, Bv, p.ws + L.cls, C_row_ptr, C_col, C_val, capacity,
+                         (unsigned long long*)(p.ws + L.fused), p.ctr, s, p.spin_limit, p.drop_tile,
+                         &p.ctr->max_u_merge);
+    if (lim.warp_u > 0)
+      launch_hash_numeric(CLS_W, Av, Bv, lw, m, C_row_ptr, C_col, C_val, p.ctr, s, lim.warp_u, p.wopt, cnt_dev + CLS_W);
+    if (lim.block_u > 0)
+      launch_hash_numeric(CLS_B, Av, Bv, lb, m, C_row_ptr, C_col, C_val, p.ctr, s, lim.block_u, p.wopt, cnt_dev + CLS_B);
+    launch_dense_numeric(Av, Bv, lg, m, p.ws + L.slabs, p.nslabs, C_row_ptr, C_col, C_val, p.ctr, s, cnt_dev + CLS_G);
+  }
+  if (cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  if (read_counters(&p, s) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  *products = (int64_t)p.h.F;
+  *nnz_c = m == 0 ? 0 : p.h.nnzC;
+  return status_from_bits(p.h.status);
 }
 
 spgemm_status_t spgemm_symbolic(spgemm_plan_t p, int32_t* C_row_ptr, int64_t* nnz_c, void* stream) {

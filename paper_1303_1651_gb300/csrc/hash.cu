@@ -168,7 +168,9 @@ __device__ __forceinline__ int warp_max_i(int v) { return __reduce_max_sync(FULL
 template <bool NUM, int U>
 __global__ void __launch_bounds__(WR_WARPS * 32, 1)
 k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __restrict__ rp,
-           int* __restrict__ C_col, double* __restrict__ C_val, Counters* __restrict__ ctr, WarpOrder wo) {
+           int* __restrict__ C_col, double* __restrict__ C_val, Counters* __restrict__ ctr, WarpOrder wo,
+           const int* __restrict__ count_dev) {
+  if (count_dev) count = *count_dev;   // the row count as the binning pass left it on the device
   using L = WarpRowSmem<NUM, U>;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -423,9 +425,8 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
 // B has at most BB_WINDOW columns the window starts at column 0 and the first pass (the row's
 // smallest column) is skipped.
 // ---------------------------------------------------------------------------
-constexpr int BB_THREADS = 512;
-constexpr int BB_WARPS = BB_THREADS / 32;
 constexpr int BB_WINDOW = 1 << 18;   // columns covered by one bit vector (bb_words)
+constexpr int BB_MAX_WARPS = 16;     // the largest block: 512 threads
 
 // words of the bit vector: one window, or all of B's columns when they are fewer
 __host__ __device__ inline int bb_words(int ncols) {
@@ -435,10 +436,11 @@ __host__ __device__ inline int bb_words(int ncols) {
 
 size_t block_bitvec_smem(int ncols, int sums, bool num) {
   const size_t words = (size_t)bb_words(ncols);
-  return (num ? 8 * (size_t)sums : 0) + 4 * words + (2 * words + 15) / 16 * 16 + 4 * 4 * BB_WARPS;
+  return (num ? 8 * (size_t)sums : 0) + 4 * words + (2 * words + 15) / 16 * 16 + 4 * 4 * BB_MAX_WARPS;
 }
 
 // Block minimum and maximum (reduction slots red[0 .. 2 * BB_WARPS)).
+template <int BB_WARPS>
 __device__ __forceinline__ void bb_minmax(int& mn, int& mx, int* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   mn = __reduce_min_sync(FULL, mn);
@@ -451,10 +453,14 @@ __device__ __forceinline__ void bb_minmax(int& mn, int& mx, int* red) {
   __syncthreads();   // red is reused
 }
 
-template <bool NUM>
+template <bool NUM, int BB_THREADS>
 __global__ void __launch_bounds__(BB_THREADS)
 k_block_bitvec(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int sums_cap, int* __restrict__ rp,
-               int* __restrict__ C_col, double* __restrict__ C_val, Counters* __restrict__ ctr) {
+               int* __restrict__ C_col, double* __restrict__ C_val, Counters* __restrict__ ctr,
+               const int* __restrict__ count_dev) {
+  if (count_dev) count = *count_dev;   // the row count as the binning pass left it on the device
+  if ((int)blockIdx.x >= count) return;   // no row for this block (uniform)
+  constexpr int BB_WARPS = BB_THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = bb_words(B.cols);
   double* sums = reinterpret_cast<double*>(smem);                                          // [sums_cap] (NUM)
@@ -480,7 +486,7 @@ k_block_bitvec(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int 
         const int bs = __ldg(B.rp + j), be = __ldg(B.rp + j + 1);
         for (int q = bs + lane; q < be; q += 32) mn = min(mn, __ldg(B.col + q));
       }
-      bb_minmax(mn, mx, red);
+      bb_minmax<BB_WARPS>(mn, mx, red);
       lo = mn;
     }
     int done = 0;   // entries of the row in the windows before this one
@@ -503,7 +509,7 @@ k_block_bitvec(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int 
       }
       {
         int nmin = next, wmx = wmax;
-        bb_minmax(nmin, wmx, red);   // red[0..]: next window (min), this window's largest (max)
+        bb_minmax<BB_WARPS>(nmin, wmx, red);   // red[0..]: next window (min), this window's largest (max)
         next = nmin;
         wmax = wmx;
       }
@@ -586,53 +592,62 @@ k_block_bitvec(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int 
 
 int block_bitvec_window() { return BB_WINDOW; }
 
+template <bool NUM, int THREADS>
+static void launch_block_bitvec_t(const DevCsr& A, const DevCsr& B, const int* list, int count, int sums_cap, int* rp,
+                                  int* C_col, double* C_val, Counters* ctr, cudaStream_t s, const int* count_dev) {
+  const size_t bytes = block_bitvec_smem(B.cols, sums_cap, NUM);
+  auto kern = k_block_bitvec<NUM, THREADS>;
+  const int per_sm = blocks_per_sm((const void*)kern, THREADS, bytes);
+  const int blocks = std::max(1, std::min(count, num_sms() * per_sm));
+  kern<<<blocks, THREADS, bytes, s>>>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, count_dev);
+}
+
+// The block takes about eight products per thread: 128 threads for rows of up to 1024 products,
+// 256 up to 2048, 512 beyond (umax: the longest row of the launch).
 template <bool NUM>
 static void launch_block_bitvec(const DevCsr& A, const DevCsr& B, const int* list, int count, int umax, int* rp,
-                                int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
+                                int* C_col, double* C_val, Counters* ctr, cudaStream_t s, const int* count_dev) {
   if (count <= 0) return;
   const int sums_cap = std::max(1, std::min(umax, BB_MAX_U));
-  const size_t bytes = block_bitvec_smem(B.cols, sums_cap, NUM);
-  auto kern = k_block_bitvec<NUM>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BB_THREADS, bytes);
-  const int blocks = std::max(1, std::min(count, num_sms() * std::max(per_sm, 1)));
-  kern<<<blocks, BB_THREADS, bytes, s>>>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr);
+  if (umax <= 1024) launch_block_bitvec_t<NUM, 128>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
+  else if (umax <= 2048) launch_block_bitvec_t<NUM, 256>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
+  else launch_block_bitvec_t<NUM, 512>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
 }
 
 template <bool NUM, int U>
 static void launch_warp_row_u(const DevCsr& A, const DevCsr& B, const int* list, int count, int* rp, int* C_col,
-                              double* C_val, Counters* ctr, cudaStream_t s, WarpOrder wo) {
+                              double* C_val, Counters* ctr, cudaStream_t s, WarpOrder wo, const int* count_dev) {
   constexpr size_t bytes = (size_t)WR_WARPS * WarpRowSmem<NUM, U>::bytes;
   auto kern = k_warp_row<NUM, U>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WR_WARPS * 32, bytes);
-  const int blocks = std::max(1, std::min((count + WR_WARPS - 1) / WR_WARPS, num_sms() * std::max(per_sm, 1)));
-  kern<<<blocks, WR_WARPS * 32, bytes, s>>>(A, B, list, count, rp, C_col, C_val, ctr, wo);
+  const int per_sm = blocks_per_sm((const void*)kern, WR_WARPS * 32, bytes);
+  const int blocks = std::max(1, std::min((count + WR_WARPS - 1) / WR_WARPS, num_sms() * per_sm));
+  kern<<<blocks, WR_WARPS * 32, bytes, s>>>(A, B, list, count, rp, C_col, C_val, ctr, wo, count_dev);
 }
 
 // umax: the longest W row (products); the smallest bound U >= umax is launched
 template <bool NUM>
 static void launch_warp_row(const DevCsr& A, const DevCsr& B, const int* list, int count, int umax, int* rp,
-                            int* C_col, double* C_val, Counters* ctr, cudaStream_t s, WarpOrder wo) {
+                            int* C_col, double* C_val, Counters* ctr, cudaStream_t s, WarpOrder wo,
+                            const int* count_dev) {
   if (count <= 0) return;
   wo.bitvec_ratio = std::max(1, std::min(wo.bitvec_ratio, 128));
-  if (umax <= 128) launch_warp_row_u<NUM, 128>(A, B, list, count, rp, C_col, C_val, ctr, s, wo);
-  else if (umax <= 256) launch_warp_row_u<NUM, 256>(A, B, list, count, rp, C_col, C_val, ctr, s, wo);
-  else launch_warp_row_u<NUM, WR_UMAX>(A, B, list, count, rp, C_col, C_val, ctr, s, wo);
+  if (umax <= 128) launch_warp_row_u<NUM, 128>(A, B, list, count, rp, C_col, C_val, ctr, s, wo, count_dev);
+  else if (umax <= 256) launch_warp_row_u<NUM, 256>(A, B, list, count, rp, C_col, C_val, ctr, s, wo, count_dev);
+  else launch_warp_row_u<NUM, WR_UMAX>(A, B, list, count, rp, C_col, C_val, ctr, s, wo, count_dev);
 }
 
 void launch_hash_symbolic(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts,
-                          Counters* ctr, cudaStream_t s, int umax, WarpOrder wo) {
-  if (cls == CLS_W) launch_warp_row<false>(A, B, list, count, umax, counts, nullptr, nullptr, ctr, s, wo);
-  else launch_block_bitvec<false>(A, B, list, count, umax, counts, nullptr, nullptr, ctr, s);
+                          Counters* ctr, cudaStream_t s, int umax, WarpOrder wo, const int* count_dev) {
+  if (cls == CLS_W) launch_warp_row<false>(A, B, list, count, umax, counts, nullptr, nullptr, ctr, s, wo, count_dev);
+  else launch_block_bitvec<false>(A, B, list, count, umax, counts, nullptr, nullptr, ctr, s, count_dev);
 }
 
 void launch_hash_numeric(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, const int* rp,
-                         int* C_col, double* C_val, Counters* ctr, cudaStream_t s, int umax, WarpOrder wo) {
-  if (cls == CLS_W) launch_warp_row<true>(A, B, list, count, umax, const_cast<int*>(rp), C_col, C_val, ctr, s, wo);
-  else launch_block_bitvec<true>(A, B, list, count, umax, const_cast<int*>(rp), C_col, C_val, ctr, s);
+                         int* C_col, double* C_val, Counters* ctr, cudaStream_t s, int umax, WarpOrder wo,
+                         const int* count_dev) {
+  if (cls == CLS_W)
+    launch_warp_row<true>(A, B, list, count, umax, const_cast<int*>(rp), C_col, C_val, ctr, s, wo, count_dev);
+  else launch_block_bitvec<true>(A, B, list, count, umax, const_cast<int*>(rp), C_col, C_val, ctr, s, count_dev);
 }
 
 // ---------------------------------------------------------------------------
@@ -662,13 +677,18 @@ template <bool NUM>
 __global__ void __launch_bounds__(G_THREADS)
 k_dense(DevCsr A, DevCsr B, const int* __restrict__ list, int count, unsigned char* slabs, size_t slab_bytes,
         int* __restrict__ counts, const int* __restrict__ rp, int* __restrict__ C_col, double* __restrict__ C_val,
-        Counters* __restrict__ ctr) {
+        Counters* __restrict__ ctr, const int* __restrict__ count_dev, bool zero_slab) {
   __shared__ int s_a[32], s_b[32], s_c[32];
   __shared__ int s_scan[32];
+  if (count_dev) count = *count_dev;   // the row count as the binning pass left it on the device
   const int n = B.cols;
   double* acc = reinterpret_cast<double*>(slabs + blockIdx.x * slab_bytes);
   int* flag = reinterpret_cast<int*>(acc + n);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (zero_slab && (int)blockIdx.x < count) {   // a slab not known to be clear: clear it before its first row
+    for (int x = threadIdx.x; x < n; x += G_THREADS) { acc[x] = 0.0; flag[x] = 0; }
+    __syncthreads();
+  }
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const int r = list[idx];
     const int a0 = A.rp[r], a1 = A.rp[r + 1];
@@ -721,19 +741,20 @@ k_dense(DevCsr A, DevCsr B, const int* __restrict__ list, int count, unsigned ch
 }
 
 void launch_dense_symbolic(const DevCsr& A, const DevCsr& B, const int* list, int count, void* slabs, int nslabs,
-                           int* counts, Counters* ctr, cudaStream_t s) {
+                           int* counts, Counters* ctr, cudaStream_t s, const int* count_dev, bool zero_slabs) {
   if (count <= 0 || nslabs <= 0) return;
   const int blocks = std::min(count, nslabs);
   k_dense<false><<<blocks, G_THREADS, 0, s>>>(A, B, list, count, (unsigned char*)slabs, dense_slab_bytes(B.cols),
-                                              counts, nullptr, nullptr, nullptr, ctr);
+                                              counts, nullptr, nullptr, nullptr, ctr, count_dev, zero_slabs);
 }
 
 void launch_dense_numeric(const DevCsr& A, const DevCsr& B, const int* list, int count, void* slabs, int nslabs,
-                          const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
+                          const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s,
+                          const int* count_dev) {
   if (count <= 0 || nslabs <= 0) return;
   const int blocks = std::min(count, nslabs);
   k_dense<true><<<blocks, G_THREADS, 0, s>>>(A, B, list, count, (unsigned char*)slabs, dense_slab_bytes(B.cols),
-                                             nullptr, rp, C_col, C_val, ctr);
+                                             nullptr, rp, C_col, C_val, ctr, count_dev, false);
 }
 
 }  // namespace spg

@@ -27,10 +27,11 @@ void launch_merge_numeric(int wide, int values_mode, const DevCsr& A, const DevC
 // Fused single pass: numeric for merge-class rows, C's row pointer for every row (rows of other classes
 // bring their counts in rp), entries written into C_col/C_val of `capacity` entries.  Uses ctr->ticket.
 // spin_limit: rounds of re-reads before a look-back gives up (0: the default bound); drop_tile:
-// testing only, a tile that publishes nothing (-1: none).
+// testing only, a tile that publishes nothing (-1: none).  max_u_dev: when not NULL, the launch runs
+// only if (*max_u_dev > 32) == wide on the device (both forms are launched before the host knows).
 void launch_merge_fused(int wide, int values_mode, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* rp,
                         int* C_col, double* C_val, long long capacity, unsigned long long* tile_state, Counters* ctr,
-                        cudaStream_t s, int spin_limit = 0, int drop_tile = -1);
+                        cudaStream_t s, int spin_limit = 0, int drop_tile = -1, const int* max_u_dev = nullptr);
 size_t fused_tile_state_bytes(int rows);
 
 // Ordering of the rows of class W (the per-row choice of Section IV-B's "Combined" kernel):
@@ -48,18 +49,24 @@ struct WarpOrder {
 // columns.
 constexpr int BB_MAX_U = 8192;
 int block_bitvec_window();
+// count_dev: when not NULL, the kernels read the row count there (as the binning pass left it on the
+// device) and `count` is only an upper bound that sizes the grid.
 void launch_hash_symbolic(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts,
-                          Counters* ctr, cudaStream_t s, int umax = 1024, WarpOrder wo = WarpOrder());
+                          Counters* ctr, cudaStream_t s, int umax = 1024, WarpOrder wo = WarpOrder(),
+                          const int* count_dev = nullptr);
 void launch_hash_numeric(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, const int* rp,
                          int* C_col, double* C_val, Counters* ctr, cudaStream_t s, int umax = 1024,
-                         WarpOrder wo = WarpOrder());
+                         WarpOrder wo = WarpOrder(), const int* count_dev = nullptr);
 
 // a2/a4, class G: dense accumulator slabs in global memory (one slab per CTA).
 size_t dense_slab_bytes(int ncols);
+// zero_slabs: every slab in use is cleared first (when the caller does not know them to be clear).
 void launch_dense_symbolic(const DevCsr& A, const DevCsr& B, const int* list, int count, void* slabs, int nslabs,
-                           int* counts, Counters* ctr, cudaStream_t s);
+                           int* counts, Counters* ctr, cudaStream_t s, const int* count_dev = nullptr,
+                           bool zero_slabs = false);
 void launch_dense_numeric(const DevCsr& A, const DevCsr& B, const int* list, int count, void* slabs, int nslabs,
-                          const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s);
+                          const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s,
+                          const int* count_dev = nullptr);
 
 // Transpose of A's structure (workspace of transpose_bytes(A.cols, A.nnz)): the compressed rows of
 // A^T -- T_cp (A.cols + 1), T_row (nnz: the row of A of each entry) and T_src (nnz: its position
@@ -84,6 +91,12 @@ void launch_grad_b(const DevCsr& A, const DevCsr& B, const void* tws, const int*
                    const double* W, double* dB, Counters* ctr, cudaStream_t s);
 
 int num_sms();
+
+// Resident blocks per SM of kern with `threads` threads and `smem` bytes of dynamic shared memory,
+// on the current device.  The first call for a (kernel, size) raises the kernel's dynamic
+// shared-memory limit to the size and asks the occupancy calculator; later calls reuse the answer
+// (a small product would otherwise spend more host time on these driver calls than on its kernels).
+int blocks_per_sm(const void* kern, int threads, size_t smem);
 
 // Largest B.cols the merge classes accept (their sort keys hold column << 6).
 int merge_max_cols();

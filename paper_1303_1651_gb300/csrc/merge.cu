@@ -191,7 +191,15 @@ struct MergeArgs {
   int rp_cap;                    // FUSED: min(capacity, INT_MAX), the largest row pointer entry stored
   long long spin_limit;          // FUSED: rounds of re-reads before a look-back gives up
   int drop_tile;                 // FUSED, testing: a tile that publishes nothing (-1: none)
+  const int* max_u_dev;          // FUSED: when not NULL, the largest sort-class row on the device; the
+  int want_wide;                 //   launch runs only if (*max_u_dev > 32) == want_wide
 };
+
+// A fused launch made before the host knows the tile form: it runs only if its form is the one
+// the binning pass chose (one of the two launched forms returns at once; uniform across the grid).
+__device__ __forceinline__ bool fused_form_selected(const MergeArgs& g) {
+  return !g.max_u_dev || ((*g.max_u_dev > 32) == (g.want_wide != 0));
+}
 
 template <int MODE, int N, int WARPS, bool DIRECT, bool RK>
 __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigned char* wb) {
@@ -861,6 +869,7 @@ k_merge_pair(MergeArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int ntiles = (g.A.rows + PairSmem<MODE>::ROWS - 1) / PairSmem<MODE>::ROWS;
+  if (MODE == MODE_FUSED && !fused_form_selected(g)) return;
   if (MODE != MODE_FUSED) {
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       merge_tile_pair<MODE>(g, tile, smem);
@@ -882,11 +891,8 @@ template <int MODE>
 static void launch_merge_pair(const MergeArgs& g, cudaStream_t s) {
   constexpr size_t bytes = PairSmem<MODE>::bytes;
   auto kern = k_merge_pair<MODE>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   const int ntiles = (g.A.rows + PairSmem<MODE>::ROWS - 1) / PairSmem<MODE>::ROWS;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, bytes);
-  if (per_sm < 1) per_sm = 1;
+  const int per_sm = blocks_per_sm((const void*)kern, 32, bytes);
   const int blocks = std::max(1, std::min(ntiles, num_sms() * per_sm * (MODE == MODE_FUSED ? 1 : 4)));
   kern<<<blocks, 32, bytes, s>>>(g);
 }
@@ -900,6 +906,7 @@ k_merge(MergeArgs g) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* wb = smem + (size_t)warp * SortSmem<MODE, N, DIRECT>::bytes;
   const int ntiles = (g.A.rows + 31) >> 5;
+  if (MODE == MODE_FUSED && !fused_form_selected(g)) return;
   if (MODE != MODE_FUSED) {
     for (int tile = blockIdx.x * WARPS + warp; tile < ntiles; tile += gridDim.x * WARPS) {
       merge_tile<MODE, N, WARPS, DIRECT, RK>(g, tile, wb);
@@ -927,11 +934,8 @@ static void launch_merge(const MergeArgs& g, cudaStream_t s) {
   constexpr bool RK_FORM = N == 32 && DIRECT;
   auto kern = (RK_FORM && g.B.cols <= (1 << 24) - 2) ? k_merge<MODE, N, WARPS, DIRECT, RK_FORM>
                                                       : k_merge<MODE, N, WARPS, DIRECT, false>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   const int ntiles = (g.A.rows + 31) / 32;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, bytes);
-  if (per_sm < 1) per_sm = 1;
+  const int per_sm = blocks_per_sm((const void*)kern, WARPS * 32, bytes);
   int blocks;
   if (MODE == MODE_FUSED) {
     blocks = std::max(1, std::min((ntiles + WARPS - 1) / WARPS, num_sms() * per_sm));
@@ -948,14 +952,14 @@ size_t fused_tile_state_bytes(int rows) { return (size_t)((rows + 15) / 16) * si
 
 void launch_merge_symbolic(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* counts,
                            Counters* ctr, cudaStream_t s) {
-  MergeArgs g{A, B, rowcls, counts, nullptr, nullptr, 0, nullptr, ctr, 0, 0, -1};
+  MergeArgs g{A, B, rowcls, counts, nullptr, nullptr, 0, nullptr, ctr, 0, 0, -1, nullptr, 0};
   if (!wide) launch_merge<MODE_SYM, 32, 4>(g, s);
   else launch_merge<MODE_SYM, 64, 4>(g, s);
 }
 
 void launch_merge_numeric(int wide, int values_mode, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls,
                           const int* rp, int* C_col, double* C_val, Counters* ctr, cudaStream_t s) {
-  MergeArgs g{A, B, rowcls, const_cast<int*>(rp), C_col, C_val, 0, nullptr, ctr, 0, 0, -1};
+  MergeArgs g{A, B, rowcls, const_cast<int*>(rp), C_col, C_val, 0, nullptr, ctr, 0, 0, -1, nullptr, 0};
   const bool direct = values_mode == 1 || (values_mode == 0 && !wide);
   if (direct) {
     if (!wide) launch_merge<MODE_NUM, 32, 1, true>(g, s);
@@ -968,10 +972,10 @@ void launch_merge_numeric(int wide, int values_mode, const DevCsr& A, const DevC
 
 void launch_merge_fused(int wide, int values_mode, const DevCsr& A, const DevCsr& B, const uint8_t* rowcls, int* rp,
                         int* C_col, double* C_val, long long capacity, unsigned long long* tile_state, Counters* ctr,
-                        cudaStream_t s, int spin_limit, int drop_tile) {
+                        cudaStream_t s, int spin_limit, int drop_tile, const int* max_u_dev) {
   MergeArgs g{A, B, rowcls, rp, C_col, C_val, capacity, tile_state, ctr,
               (int)std::min(capacity, (long long)INT_MAX), spin_limit > 0 ? (long long)spin_limit : FUSED_SPIN_LIMIT,
-              drop_tile};
+              drop_tile, max_u_dev, wide};
   const bool direct = values_mode == 1 || (values_mode == 0 && !wide);
   if (direct) {
     if (!wide) launch_merge<MODE_FUSED, 32, 1, true>(g, s);

@@ -1,4 +1,8 @@
 // a1 row binning and a3 exclusive scan.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "internal.h"
 
 namespace spg {
@@ -12,6 +16,28 @@ int num_sms() {
     if (n <= 0) n = 1;
   }
   return n;
+}
+
+int blocks_per_sm(const void* kern, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_tuple(dev, kern, threads, smem);
+  const auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  size_t& lim = limit[std::make_pair(dev, kern)];
+  if (smem > lim) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    lim = smem;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  cache[key] = per_sm;
+  return per_sm;
 }
 
 // ---------------------------------------------------------------------------
@@ -162,11 +188,7 @@ void launch_bin(const DevCsr& A, const DevCsr& B, const Limits& lim_in, uint8_t*
   if (A.rows <= 0) return;
   Limits lim = lim_in;
   if (B.cols > merge_max_cols()) { lim.m1_u = -1; lim.m2_u = -1; }   // sort keys hold column << log2(N)
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin, BIN_THREADS, 0);
-    if (per_sm < 1) per_sm = 1;
-  }
+  const int per_sm = blocks_per_sm((const void*)k_bin, BIN_THREADS, 0);
   const long long need = ((long long)A.rows + (long long)BIN_THREADS * BIN_ROWS - 1) / ((long long)BIN_THREADS * BIN_ROWS);
   const int grid = (int)std::max(1LL, std::min(need, (long long)num_sms() * per_sm));
   k_bin<<<grid, BIN_THREADS, 0, s>>>(A, B, lim, cls, lists[0], lists[1], lists[2], lists[3], lists[4], ctr);

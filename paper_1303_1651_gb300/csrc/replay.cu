@@ -203,14 +203,12 @@ void launch_replay(int wide, const DevCsr& A, const DevCsr& B, const uint8_t* cl
   const int* tile_off = (const int*)map;
   const uint8_t* bytes = (const uint8_t*)map + (4 * ((size_t)ntiles + 1) + 255) / 256 * 256;
   if (!wide) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_replay<32>, 32, 0);
-    const int grid = std::max(1, std::min(ntiles, num_sms() * std::max(per_sm, 1)));
+    const int per_sm = blocks_per_sm((const void*)k_replay<32>, 32, 0);
+    const int grid = std::max(1, std::min(ntiles, num_sms() * per_sm));
     k_replay<32><<<grid, 32, 0, s>>>(A, B, cls, C_rp, tile_off, bytes, C_val);
   } else {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_replay<64>, 32, 0);
-    const int grid = std::max(1, std::min(ntiles, num_sms() * std::max(per_sm, 1)));
+    const int per_sm = blocks_per_sm((const void*)k_replay<64>, 32, 0);
+    const int grid = std::max(1, std::min(ntiles, num_sms() * per_sm));
     k_replay<64><<<grid, 32, 0, s>>>(A, B, cls, C_rp, tile_off, bytes, C_val);
   }
 }
