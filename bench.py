@@ -802,10 +802,11 @@ def run_long_rows(args, dev, binding, torch):
     bw, _ = hbm_peak()
     steps = max(3, min(args.steps, 10))
     off = dict(m1_max_u=-1, m2_max_u=-1)
-    variants = [("default", {}), ("W", off), ("B", dict(off, warp_max_u=-1)),
+    offw = dict(off, warp_max_u=1024)
+    variants = [("default", {}), ("W", offw), ("B", dict(off, warp_max_u=-1)),
                 ("G", dict(off, warp_max_u=-1, block_max_u=-1)),
-                ("W-minmax", dict(off, warp_order=1)), ("W-sort", dict(off, warp_order=2)),
-                ("W-hash", dict(off, warp_order=3))]
+                ("W-minmax", dict(offw, warp_order=1)), ("W-sort", dict(offw, warp_order=2)),
+                ("W-hash", dict(offw, warp_order=3))]
     out = {"fill": 0.001, "points": []}
     for N in (5000, 10000, 20000, 30000, 38000, 50000, 70000):
         A = synth.random_fill(N, 0.001, synth.SEED_A + N)

@@ -110,7 +110,7 @@ typedef struct {
                              register sort across the warp when the range fits its 32-bit keys:
                              below 2^25 for u_r <= 128 down to 2^22 for u_r > 512, and for u_r <= 32
                              below 2^22 only; else a hash table): u_r <= this (max 1024, default
-                             1024) */
+                             256; longer rows run faster in class B) */
   int32_t block_max_u;    /* block-per-row class B (the row's columns ordered by a bit vector over
                              windows of 2^18 columns, one window after another): u_r <= this (max
                              8192, default 8192); longer rows use a dense accumulator in global
@@ -254,6 +254,23 @@ spgemm_status_t spgemm_compute_async(spgemm_plan_t plan, const double* A_val, co
 spgemm_status_t spgemm_multiply(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
                                 void* workspace, size_t workspace_bytes, int32_t* C_row_ptr, int32_t* C_col,
                                 double* C_val, int64_t capacity, int64_t* nnz_c, int64_t* products, void* stream);
+
+/* spgemm_multiply without the host synchronisation: the work is only enqueued on stream, and
+ * nnz(C), F and the status stay in the workspace's counters, where spgemm_multiply_result reads
+ * them.  Nothing the call enqueues depends on the data on the host side (every class kernel reads
+ * its row count on the device), so the call can be captured into a CUDA graph once (after one
+ * eager call, which sets the kernels' attributes) and the graph replayed for new contents of the
+ * same arrays: a product of the same shapes per replay, with one read-back.  Errors: INVALID,
+ * ALLOC, CUDA (host checks and launches; device errors are reported by spgemm_multiply_result). */
+spgemm_status_t spgemm_multiply_async(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
+                                      void* workspace, size_t workspace_bytes, int32_t* C_row_ptr, int32_t* C_col,
+                                      double* C_val, int64_t capacity, void* stream);
+
+/* Synchronise stream and read the counters that the last spgemm_multiply_async on `workspace` left
+ * there: nnz(C) and F (host, always written), and the status (OK, OVERFLOW when nnz(C) passed the
+ * capacity or INT32_MAX, TABLE_FULL, TIMEOUT, INVALID).  Errors: INVALID (NULL or misaligned
+ * workspace), CUDA. */
+spgemm_status_t spgemm_multiply_result(const void* workspace, int64_t* nnz_c, int64_t* products, void* stream);
 
 /* Pattern reuse: new values of A and B, the same structures, C's structure kept.
  *

@@ -86,6 +86,9 @@ def load():
         lib.spgemm_replay.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.spgemm_multiply.argtypes = [P(spgemm_csr_t), P(spgemm_csr_t), P(spgemm_options_t), vp, ctypes.c_size_t,
                                         vp, vp, vp, ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_int64), vp]
+        lib.spgemm_multiply_async.argtypes = [P(spgemm_csr_t), P(spgemm_csr_t), P(spgemm_options_t), vp,
+                                              ctypes.c_size_t, vp, vp, vp, ctypes.c_int64, vp]
+        lib.spgemm_multiply_result.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64), vp]
         lib.spgemm_error_string.argtypes = [ctypes.c_int]
         lib.spgemm_error_string.restype = ctypes.c_char_p
         lib.spgemm_version.restype = ctypes.c_int32
@@ -93,7 +96,8 @@ def load():
                      "spgemm_compute", "spgemm_status", "spgemm_plan_info", "spgemm_free",
                      "spgemm_plan_set_events", "spgemm_compute_async", "spgemm_backward_workspace_size",
                      "spgemm_backward", "spgemm_scan_counts_noalloc", "spgemm_replay_size",
-                     "spgemm_replay_record", "spgemm_replay", "spgemm_multiply"):
+                     "spgemm_replay_record", "spgemm_replay", "spgemm_multiply", "spgemm_multiply_async",
+                     "spgemm_multiply_result"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -314,6 +318,58 @@ def spgemm_multiply(A, B, C_row_ptr: torch.Tensor, C_col: torch.Tensor, C_val: t
         return int(nnz.value), int(F.value)
     _check(code, "spgemm_multiply")
     return int(nnz.value), int(F.value)
+
+
+def spgemm_multiply_async(A, B, C_row_ptr: torch.Tensor, C_col: torch.Tensor, C_val: torch.Tensor,
+                          workspace: torch.Tensor, opt: spgemm_options_t | None = None, stream=None):
+    """Enqueue spgemm_multiply's work without synchronising (CUDA-graph capturable); read the result
+    with spgemm_multiply_result(workspace)."""
+    opt = with_storage(A, B, opt)
+    a, b = A.desc(True), B.desc(True)
+    cap = min(C_col.numel(), C_val.numel())
+    _check(load().spgemm_multiply_async(ctypes.byref(a), ctypes.byref(b), ctypes.byref(opt) if opt else None,
+                                        workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                        C_row_ptr.data_ptr(), _ptr(C_col), _ptr(C_val), cap, _stream(stream)),
+           "spgemm_multiply_async")
+
+
+def spgemm_multiply_result(workspace: torch.Tensor, stream=None, raise_on_overflow: bool = True):
+    """(nnz(C), F) left in the workspace by the last spgemm_multiply_async on it (synchronises)."""
+    nnz, F = ctypes.c_int64(0), ctypes.c_int64(0)
+    code = load().spgemm_multiply_result(workspace.data_ptr(), ctypes.byref(nnz), ctypes.byref(F), _stream(stream))
+    if not (code == 3 and not raise_on_overflow):
+        _check(code, "spgemm_multiply_result")
+    return int(nnz.value), int(F.value)
+
+
+class GraphProduct:
+    """C = A*B for arrays whose shapes stay fixed, from a CUDA graph of spgemm_multiply_async: each
+    run() replays binning and the single-pass product over the arrays' current contents (no host
+    work between its kernels) and reads nnz(C) and F back once.  C holds `capacity` entries."""
+
+    def __init__(self, A, B, capacity: int, opt: spgemm_options_t | None = None):
+        self.A, self.B, self.opt = A, B, with_storage(A, B, opt)
+        dev = A.val.device
+        self.ws = torch.empty(spgemm_workspace_size(A, B, self.opt), dtype=torch.uint8, device=dev)
+        self.C_row_ptr = torch.empty(A.rows + 1, dtype=torch.int32, device=dev)
+        self.C_col = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+        self.C_val = torch.empty(max(capacity, 1), dtype=torch.float64, device=dev)
+        self._enqueue()                       # eager: kernel attributes set before the capture
+        spgemm_multiply_result(self.ws, raise_on_overflow=False)
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=side):
+            self._enqueue()
+        torch.cuda.current_stream(dev).wait_stream(side)
+
+    def _enqueue(self):
+        spgemm_multiply_async(self.A, self.B, self.C_row_ptr, self.C_col, self.C_val, self.ws, self.opt)
+
+    def run(self, raise_on_overflow: bool = True):
+        """Replay; returns (nnz(C), F)."""
+        self.graph.replay()
+        return spgemm_multiply_result(self.ws, raise_on_overflow=raise_on_overflow)
 
 
 def multiply_once(A, B, opt: spgemm_options_t | None = None, stream=None, capacity: int | None = None,

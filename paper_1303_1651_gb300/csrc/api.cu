@@ -50,7 +50,9 @@ Layout layout(const spgemm_csr_t& A, const spgemm_csr_t& B, int nslabs, const bo
 }
 
 Limits limits_from(const spgemm_options_t* o) {
-  Limits l{8, 32, 64, 1024, 0};
+  // Class W takes rows of up to 256 products by default: longer rows run faster in class B's
+  // bit-vector blocks (measured on the batched workload and on the 0.1 % fill rows).
+  Limits l{8, 32, 64, 256, 0};
   if (o) {
     if (o->merge_max_k > 0) l.merge_k = std::min(o->merge_max_k, 8);
     if (o->m1_max_u > 0) l.m1_u = std::min(o->m1_max_u, 32);
@@ -357,10 +359,13 @@ spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spg
 // row count on the device (a class with no rows costs an empty launch), the dense slabs are cleared
 // by their kernel, and both tile forms of the fused pass are launched (the one the binning did not
 // choose returns at once).  The counters are read back once, at the end.
-spgemm_status_t spgemm_multiply(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
-                                void* workspace, size_t workspace_bytes, int32_t* C_row_ptr, int32_t* C_col,
-                                double* C_val, int64_t capacity, int64_t* nnz_c, int64_t* products, void* stream) {
-  if (!nnz_c || !products || !C_row_ptr || capacity < 0) return SPGEMM_ERR_INVALID;
+// Enqueue spgemm_multiply's work on s (p: a plan object on the caller's stack, holding no pinned
+// slot unless the caller gave it one).  Host checks only; nothing is read back.
+static spgemm_status_t multiply_enqueue(spgemm_plan_s& p, const spgemm_csr_t* A, const spgemm_csr_t* B,
+                                        const spgemm_options_t* opt, void* workspace, size_t workspace_bytes,
+                                        int32_t* C_row_ptr, int32_t* C_col, double* C_val, int64_t capacity,
+                                        cudaStream_t s) {
+  if (!C_row_ptr || capacity < 0) return SPGEMM_ERR_INVALID;
   if ((!C_col || !C_val) && capacity > 0) return SPGEMM_ERR_INVALID;
   bool csc[2];
   int nslabs = 0;
@@ -369,9 +374,6 @@ spgemm_status_t spgemm_multiply(const spgemm_csr_t* A, const spgemm_csr_t* B, co
   if (a != SPGEMM_OK) return a;
   if ((!A->val && A->nnz > 0) || (!B->val && B->nnz > 0)) return SPGEMM_ERR_INVALID;
   if (fault_is("nnz_overflow")) capacity = 0;
-  cudaStream_t s = (cudaStream_t)stream;
-  spgemm_plan_s p;
-  p.pinned = pinned_take();
   plan_enqueue(&p, A, B, opt, workspace, csc, nslabs, L, s);
   const int m = p.A.rows;
   if (m == 0) {
@@ -400,10 +402,43 @@ spgemm_status_t spgemm_multiply(const spgemm_csr_t* A, const spgemm_csr_t* B, co
       launch_hash_numeric(CLS_B, Av, Bv, lb, m, C_row_ptr, C_col, C_val, p.ctr, s, lim.block_u, p.wopt, cnt_dev + CLS_B);
     launch_dense_numeric(Av, Bv, lg, m, p.ws + L.slabs, p.nslabs, C_row_ptr, C_col, C_val, p.ctr, s, cnt_dev + CLS_G);
   }
-  if (cudaGetLastError() != cudaSuccess) return SPGEMM_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
+}
+
+spgemm_status_t spgemm_multiply(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
+                                void* workspace, size_t workspace_bytes, int32_t* C_row_ptr, int32_t* C_col,
+                                double* C_val, int64_t capacity, int64_t* nnz_c, int64_t* products, void* stream) {
+  if (!nnz_c || !products) return SPGEMM_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  spgemm_plan_s p;
+  p.pinned = pinned_take();
+  const spgemm_status_t e = multiply_enqueue(p, A, B, opt, workspace, workspace_bytes, C_row_ptr, C_col, C_val,
+                                             capacity, s);
+  if (e != SPGEMM_OK) return e;
   if (read_counters(&p, s) != cudaSuccess) return SPGEMM_ERR_CUDA;
   *products = (int64_t)p.h.F;
-  *nnz_c = m == 0 ? 0 : p.h.nnzC;
+  *nnz_c = p.A.rows == 0 ? 0 : p.h.nnzC;
+  return status_from_bits(p.h.status);
+}
+
+spgemm_status_t spgemm_multiply_async(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
+                                      void* workspace, size_t workspace_bytes, int32_t* C_row_ptr, int32_t* C_col,
+                                      double* C_val, int64_t capacity, void* stream) {
+  spgemm_plan_s p;
+  return multiply_enqueue(p, A, B, opt, workspace, workspace_bytes, C_row_ptr, C_col, C_val, capacity,
+                          (cudaStream_t)stream);
+}
+
+spgemm_status_t spgemm_multiply_result(const void* workspace, int64_t* nnz_c, int64_t* products, void* stream) {
+  if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || !nnz_c || !products) return SPGEMM_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  spgemm_plan_s p;
+  p.pinned = pinned_take();
+  p.ws = (unsigned char*)const_cast<void*>(workspace);
+  p.ctr = (Counters*)p.ws;   // the counters open every workspace (Layout::ctr is 0)
+  if (read_counters(&p, s) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  *products = (int64_t)p.h.F;
+  *nnz_c = p.h.nnzC;
   return status_from_bits(p.h.status);
 }
 

@@ -409,9 +409,10 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
 // ---------------------------------------------------------------------------
 // Class B: one block of 512 threads per row, its columns ordered by a bit vector -- the MinMax
 // store of Section IV-B with the flags as bits, kept in shared memory; no hash table, no sort.
-// The bit vector covers a window of BB_WINDOW columns above the row's smallest column not yet
-// done; a row whose columns span more is done window by window, each window starting at the
-// smallest column past the last.  Per window:
+// The bit vector covers a window of columns above the row's smallest column not yet done: all of B
+// when B has at most BB_WINDOW columns, else BB_WIDE_WINDOW columns (a block then holds little
+// shared memory and many blocks fit an SM); a row whose columns span more is done window by window,
+// each window starting at the smallest column past the last.  Per window:
 //   1. mark  -- each product in the window sets its column's bit (a warp per entry of A, lanes
 //               along the row of B); the window's largest column and the next window's first
 //               column come out of the same pass;
@@ -425,13 +426,14 @@ k_warp_row(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int* __r
 // B has at most BB_WINDOW columns the window starts at column 0 and the first pass (the row's
 // smallest column) is skipped.
 // ---------------------------------------------------------------------------
-constexpr int BB_WINDOW = 1 << 18;   // columns covered by one bit vector (bb_words)
+constexpr int BB_WINDOW = 1 << 18;        // B up to this many columns: one window over all of B
+constexpr int BB_WIDE_WINDOW = 1 << 16;   // wider B: windows of this many columns
 constexpr int BB_MAX_WARPS = 16;     // the largest block: 512 threads
 
-// words of the bit vector: one window, or all of B's columns when they are fewer
+// words of the bit vector: all of B's columns when they are at most BB_WINDOW, else BB_WIDE_WINDOW
 __host__ __device__ inline int bb_words(int ncols) {
   const int n = ncols < 1 ? 1 : ncols;
-  return ((n < (1 << 18) ? n : (1 << 18)) + 31) / 32;
+  return ((n <= (1 << 18) ? n : (1 << 16)) + 31) / 32;
 }
 
 size_t block_bitvec_smem(int ncols, int sums, bool num) {
@@ -469,6 +471,7 @@ k_block_bitvec(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int 
   int* red = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(rank) + ((size_t)2 * W + 15) / 16 * 16);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool one_window = B.cols <= BB_WINDOW;
+  const int win = one_window ? 32 * W : BB_WIDE_WINDOW;   // columns per window
   for (int w = tid; w < W; w += BB_THREADS) bits[w] = 0u;
   __syncthreads();
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
@@ -491,7 +494,7 @@ k_block_bitvec(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int 
     }
     int done = 0;   // entries of the row in the windows before this one
     while (lo != INT_MAX) {   // block-uniform
-      const long long hi = (long long)lo + BB_WINDOW;   // window [lo, hi)
+      const long long hi = (long long)lo + win;   // window [lo, hi)
       // 1. mark
       int wmax = INT_MIN, next = INT_MAX;
       for (int e = a0 + warp; e < a1; e += BB_WARPS) {
@@ -589,8 +592,6 @@ k_block_bitvec(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int 
     }
   }
 }
-
-int block_bitvec_window() { return BB_WINDOW; }
 
 template <bool NUM, int THREADS>
 static void launch_block_bitvec_t(const DevCsr& A, const DevCsr& B, const int* list, int count, int sums_cap, int* rp,

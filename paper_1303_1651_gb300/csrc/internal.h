@@ -45,12 +45,9 @@ struct WarpOrder {
 
 // a2/a4, classes W (warp per row) and B (block per row), rows from a list.  umax: the longest row
 // of the class (W: sizes the W kernel's shared memory; B: the sums of its bit-vector windows, at
-// most BB_MAX_U).  Class B orders each row by a bit vector over windows of block_bitvec_window()
-// columns.
+// most BB_MAX_U, and the block size).  Class B orders each row by a bit vector over windows of
+// columns (all of B when B has at most 2^18 columns, else 2^16 columns per window).
 constexpr int BB_MAX_U = 8192;
-int block_bitvec_window();
-// count_dev: when not NULL, the kernels read the row count there (as the binning pass left it on the
-// device) and `count` is only an upper bound that sizes the grid.
 void launch_hash_symbolic(int cls, const DevCsr& A, const DevCsr& B, const int* list, int count, int* counts,
                           Counters* ctr, cudaStream_t s, int umax = 1024, WarpOrder wo = WarpOrder(),
                           const int* count_dev = nullptr);

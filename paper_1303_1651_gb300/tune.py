@@ -32,8 +32,9 @@ CANDIDATES = [
     {"merge_max_k": 4},
     {"m1_max_u": -1, "m2_max_u": -1},             # no sort classes: every row to the warp and block classes
     # class limits (bins): rows per warp / per block before the dense accumulator
-    {"warp_max_u": 256},
+    {"warp_max_u": 128},
     {"warp_max_u": 512},
+    {"warp_max_u": 1024},
     {"block_max_u": 2048},
     # class W: the per-row ordering (Section IV-B's "Combined" switch and its alternatives)
     {"warp_bitvec_ratio": 2},                     # the paper's rule: range below twice the row

@@ -92,6 +92,6 @@ def test_warp_orderings(order, fused):
     for ncols, seed in ((1500, 471), (200_000, 472), (20_000_000, 473)):
         A = synth.random_lengths(np.random.default_rng(seed).integers(9, 33, 600), 500, seed)
         B = synth.random_lengths(np.random.default_rng(seed + 1).integers(9, 21, 500), ncols, seed + 1)
-        C = gpu_product(A, B, binding.options(m1_max_u=-1, m2_max_u=-1, **order), fused=fused)
+        C = gpu_product(A, B, binding.options(m1_max_u=-1, m2_max_u=-1, warp_max_u=1024, **order), fused=fused)
         assert C["info"]["rows_per_class"]["W"] > 500
         compare(C, oracle.spgemm(A, B), single=True)

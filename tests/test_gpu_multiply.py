@@ -112,3 +112,57 @@ def test_empty_and_csc():
     C = binding.multiply_once(dev(A), b)
     torch.cuda.synchronize()
     compare(C.to_host(), oracle.spgemm(A, Bc), single=True)
+
+
+@pytest.mark.parametrize("case", ["rand-k6", "power-law"])
+def test_graph_replay(case):
+    # spgemm_multiply_async captured once into a CUDA graph, replayed over new contents of the same
+    # arrays: new values, then a new pattern of the same sizes (other row classes, another nnz(C))
+    if case == "rand-k6":
+        mats = [(synth.random_k(6000, 6, 531 + 2 * i), synth.random_k(6000, 6, 532 + 2 * i)) for i in range(3)]
+    else:
+        mats = [(synth.power_law(2500, 2500, 41 + 2 * i, alpha=1.5, max_len=2500),
+                 synth.power_law(2500, 3000, 42 + 2 * i, alpha=1.5, max_len=600)) for i in range(3)]
+    # the same nnz for each operand in every product: the patterns are cut or padded to the first's
+    def fit(M, nnz):
+        rp = np.minimum(M.row_ptr.astype(np.int64), nnz)
+        col = M.col_idx[:nnz]
+        val = M.val[:nnz]
+        if len(col) < nnz:                          # pad the last row with repeated columns
+            pad = nnz - len(col)
+            col = np.concatenate([col, np.full(pad, M.cols - 1, np.int32)])
+            val = np.concatenate([val, np.full(pad, 0.5)])
+        rp[-1] = nnz
+        return synth.CSR(M.rows, M.cols, rp.astype(np.int32), col.astype(np.int32), val)
+    nA, nB = mats[0][0].nnz, mats[0][1].nnz
+    mats = [(fit(A, nA), fit(B, nB)) for A, B in mats]
+    dA, dB = dev(mats[0][0]), dev(mats[0][1])
+    cap = max(oracle.spgemm(A, B)["nnz"] for A, B in mats)
+    g = binding.GraphProduct(dA, dB, cap)
+    for i, (A, B) in enumerate(mats):
+        R = oracle.spgemm(A, B)
+        for X, dX in ((A, dA), (B, dB)):
+            dX.row_ptr.copy_(torch.from_numpy(X.row_ptr))
+            dX.col_idx.copy_(torch.from_numpy(X.col_idx))
+            dX.val.copy_(torch.from_numpy(X.val))
+        for rep in range(2):                        # a second replay gives the same C
+            nnz, F = g.run()
+            assert (nnz, F) == (R["nnz"], R["F"]), (i, rep)
+            got = dict(row_ptr=g.C_row_ptr.cpu().numpy(), col_idx=g.C_col[:nnz].cpu().numpy(),
+                       val=g.C_val[:nnz].cpu().numpy())
+            compare(got, R, single=True)
+        # with new values only: the numbers change, the pattern does not
+        dA.val.mul_(-2.0)
+        nnz, _ = g.run()
+        R2 = oracle.spgemm(synth.CSR(A.rows, A.cols, A.row_ptr, A.col_idx, -2.0 * A.val), B)
+        compare(dict(row_ptr=g.C_row_ptr.cpu().numpy(), col_idx=g.C_col[:nnz].cpu().numpy(),
+                     val=g.C_val[:nnz].cpu().numpy()), R2, single=True)
+
+
+def test_graph_replay_overflow_report():
+    A, B = synth.random_k(3000, 6, 541), synth.random_k(3000, 6, 542)
+    R = oracle.spgemm(A, B)
+    g = binding.GraphProduct(dev(A), dev(B), R["nnz"] // 2)
+    with pytest.raises(binding.SpgemmError, match="OVERFLOW"):
+        g.run()
+    assert g.run(raise_on_overflow=False) == (R["nnz"], R["F"])

@@ -274,7 +274,7 @@ def test_warp_class_orderings(ncols, k, fused):
     # more than 32 products take it.
     A = synth.random_k(700, k, 81, ncols=400)
     B = synth.random_k(400, k, 82, ncols=ncols)
-    C = gpu_product(A, B, opts(m1_max_u=-1, m2_max_u=-1), fused=fused)
+    C = gpu_product(A, B, opts(m1_max_u=-1, m2_max_u=-1, warp_max_u=1024), fused=fused)
     assert C["info"]["rows_per_class"]["W"] == 700
     compare(C, oracle.spgemm(A, B), single=True)
 
