@@ -1,11 +1,11 @@
 """A bounded device wait that runs out, and the host-side fault injections, on the GPU.
 
-The single-pass product places each tile of rows by a decoupled look-back over the tiles before
-it, a wait bounded by a count of re-reads.  With the testing options debug_drop_tile (a tile that
-publishes nothing) and debug_spin_limit (a short bound), the look-backs that reach the dropped
-tile give up: the call must return SPGEMM_ERR_TIMEOUT, nothing is written outside the caller's
-buffers, and the device stays usable (a normal product right after equals the oracle).  Nothing
-here faults, traps or hangs the GPU: every wait ends by its bound."""
+The single-pass product places each tile (or group of tiles) of rows by a decoupled look-back over
+the ones before it, a wait bounded by a count of re-reads.  With the testing options
+debug_drop_tile (a unit that publishes nothing) and debug_spin_limit (a short bound), the
+look-backs that reach the dropped unit give up: the call must return SPGEMM_ERR_TIMEOUT, nothing
+is written outside the caller's buffers, and the device stays usable (a normal product right after
+equals the oracle).  Nothing here faults, traps or hangs the GPU: every wait ends by its bound."""
 import pytest
 import torch
 
@@ -34,15 +34,16 @@ def fused(A, B, opt):
         binding.spgemm_free(plan)
 
 
-@pytest.mark.parametrize("k", [4, 8], ids=["32-row-tiles", "16-row-tiles"])
-def test_lookback_gives_up_and_the_device_stays_usable(k):
+@pytest.mark.parametrize("k,form", [(4, {}), (4, dict(merge_values=2)), (8, {})],
+                         ids=["128-row-groups", "32-row-tiles", "16-row-tiles"])
+def test_lookback_gives_up_and_the_device_stays_usable(k, form):
     A, B = synth.random_k(20_000, k, 481), synth.random_k(20_000, k, 482)
-    err, C_col = fused(A, B, binding.options(debug_drop_tile=1 + 100, debug_spin_limit=512))
+    err, C_col = fused(A, B, binding.options(debug_drop_tile=1 + 100, debug_spin_limit=512, **form))
     assert err == "SPGEMM_ERR_TIMEOUT"
     torch.cuda.synchronize()
     assert bool((C_col[-64:] == -7).all()), "written past the capacity"
-    # the same product without the dropped tile, on the same device, right after
-    err, _ = fused(A, B, binding.options(debug_spin_limit=512))
+    # the same product without the dropped unit, on the same device, right after
+    err, _ = fused(A, B, binding.options(debug_spin_limit=512, **form))
     assert err is None
     from tests.gpu_util import gpu_product
     compare(gpu_product(A, B, fused=True), oracle.spgemm(A, B), single=True)
