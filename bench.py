@@ -990,6 +990,29 @@ def run_sweep(args):
                 one_ms.append(e0.elapsed_time(e1))
             assert onnz == pt["nnz_c"]
             del oC_col, oC_val
+            # the same product as a CUDA graph of spgemm_multiply_async, replayed: the step is the
+            # replay and the read-back of nnz(C) (graph_ms), or the replay alone (graph_device_ms)
+            gp = binding.GraphProduct(dA, dB, cap)
+            for _ in range(W):
+                gp.run()
+            g_ms, gd_ms = [], []
+            for i in range(K):
+                flush.zero_()
+                e0, e1 = ev[2 * i]
+                d0, d1 = ev[2 * i + 1]
+                torch.cuda.synchronize()
+                e0.record(stream)
+                d0.record(stream)
+                gp.graph.replay()
+                d1.record(stream)
+                gnnz, _ = binding.spgemm_multiply_result(gp.ws, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                g_ms.append(e0.elapsed_time(e1))
+                gd_ms.append(d0.elapsed_time(d1))
+            assert gnnz == pt["nnz_c"]
+            del gp
+            pt.update({"graph_ms": float(np.median(g_ms)), "graph_device_ms": float(np.median(gd_ms))})
             bmin = roofline.bytes_min(A, B, nnz)
             ms, kms = float(np.median(step_ms)), float(np.median(kern_ms))
             oms = float(np.median(one_ms))
@@ -1012,6 +1035,8 @@ def run_sweep(args):
                        "step": "plan (binning, F read back) + single-pass compute (nnz(C) read back)",
                        "one_sync": "spgemm_multiply: binning and single-pass compute in one call, one read-back, "
                                    "C preallocated with capacity F",
+                       "graph": "spgemm_multiply_async captured once in a CUDA graph: graph_ms = replay + "
+                                "read-back of nnz(C) (spgemm_multiply_result), graph_device_ms = the replay alone",
                        "kernel": "the compute call's kernels alone (events around them)"},
             "peak": {"hbm_gbs": bw, "kind": f"{bw_kind} (MEASURED_PEAKS.json hbm_gbs)"},
             "clocks": clk.summary(), "points": points}

@@ -465,7 +465,7 @@ spgemm_status_t spgemm_symbolic(spgemm_plan_t p, int32_t* C_row_ptr, int64_t* nn
                            p->wopt);
   if (cnt[CLS_B] > 0)
     launch_hash_symbolic(CLS_B, p->A, p->B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s,
-                         p->h.max_u);
+                         p->h.max_u_b);
   if (cnt[CLS_G] > 0)
     launch_dense_symbolic(p->A, p->B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs,
                           C_row_ptr, p->ctr, s);
@@ -501,7 +501,7 @@ spgemm_status_t spgemm_numeric(spgemm_plan_t p, const double* A_val, const doubl
                         p->wopt);
   if (cnt[CLS_B] > 0)
     launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], p->C_rp, C_col, C_val, p->ctr, s,
-                        p->h.max_u);
+                        p->h.max_u_b);
   if (cnt[CLS_G] > 0)
     launch_dense_numeric(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs, p->C_rp,
                          C_col, C_val, p->ctr, s);
@@ -542,7 +542,7 @@ static spgemm_status_t compute_enqueue(spgemm_plan_t p, const double* A_val, con
                            p->wopt);
     if (cnt[CLS_B] > 0)
       launch_hash_symbolic(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, p->ctr, s,
-                           p->h.max_u);
+                           p->h.max_u_b);
     if (cnt[CLS_G] > 0)
       launch_dense_symbolic(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs,
                             C_row_ptr, p->ctr, s);
@@ -554,7 +554,7 @@ static spgemm_status_t compute_enqueue(spgemm_plan_t p, const double* A_val, con
                         p->wopt);
     if (cnt[CLS_B] > 0)
       launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], C_row_ptr, C_col, C_val, p->ctr, s,
-                          p->h.max_u);
+                          p->h.max_u_b);
     if (cnt[CLS_G] > 0)
       launch_dense_numeric(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs, C_row_ptr,
                            C_col, C_val, p->ctr, s);
@@ -632,7 +632,7 @@ spgemm_status_t spgemm_replay(spgemm_plan_t p, const double* A_val, const double
                         p->wopt);
   if (cnt[CLS_B] > 0)
     launch_hash_numeric(CLS_B, A, B, (const int*)(p->ws + L.list_b), cnt[CLS_B], p->C_rp, C_col, C_val, p->ctr, s,
-                        p->h.max_u);
+                        p->h.max_u_b);
   if (cnt[CLS_G] > 0)
     launch_dense_numeric(A, B, (const int*)(p->ws + L.list_g), cnt[CLS_G], p->ws + L.slabs, p->nslabs, p->C_rp,
                          C_col, C_val, p->ctr, s);

@@ -49,7 +49,8 @@ struct Counters {
   int max_u;                 // largest row product count
   int max_u_merge;           // largest product count among merge-class rows
   int max_u_w;               // largest product count among class-W rows
-  int pad[4];
+  int max_u_b;               // largest product count among class-B rows
+  int pad[3];
 };
 
 struct Limits {

@@ -593,6 +593,208 @@ k_block_bitvec(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Class B, rows of up to BB_STAGE_U products: the same windowed bit vector, with the row's products
+// staged in shared memory first.  The block reads the row's entries of A and the ranges of the rows
+// of B they select once (a thread per entry), then copies every product's column (and, numeric, its
+// product a_rj * b_jx) with a thread per product, all loads of the block in flight together; the
+// mark and sum passes then read shared memory instead of repeating the dependent loads.  Ranks come
+// from one block scan over runs of consecutive words, one run per thread (the runs have an odd
+// length, so the 32 lanes of a warp read 32 different banks).  The sum pass also records each
+// entry's column by its rank, so C is written (and the vector cleared) entry by entry, consecutive
+// threads on consecutive entries of C, without walking the vector's words again.
+// ---------------------------------------------------------------------------
+constexpr int BB_STAGE_U = 2048;
+
+// Shared memory of k_block_staged, in bytes: sums, products and the entries' columns (numeric),
+// a of the chunk's entries (numeric), the products' columns, bits, entry starts, entry sources,
+// reduction slots, ranks (numeric).
+struct StagedSmem {
+  size_t sums, prod, ocol, sa, scol, bits, start, src, red, rank, bytes;
+  __host__ __device__ StagedSmem(int words, int ucap, bool num, int threads) {
+    sums = 0;
+    prod = sums + (num ? 8 * (size_t)ucap : 0);
+    ocol = prod + (num ? 8 * (size_t)ucap : 0);
+    sa = ocol + (num ? 4 * (size_t)ucap : 0);
+    sa = (sa + 7) / 8 * 8;
+    scol = sa + (num ? 8 * (size_t)threads : 0);
+    bits = scol + 4 * (size_t)ucap;
+    start = bits + 4 * (size_t)words;
+    src = start + 4 * (size_t)threads;
+    red = src + 4 * (size_t)threads;
+    rank = red + 4 * 4 * (size_t)(threads / 32);
+    bytes = rank + (num ? 2 * (size_t)words : 0);
+  }
+};
+
+// Exclusive prefix of v over the block; *total gets the block's sum.  red: BB_WARPS ints.
+template <int BB_WARPS>
+__device__ __forceinline__ int bb_excl_scan(int v, int* red, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) red[warp] = incl;
+  __syncthreads();
+  int woff = 0, sum = 0;
+#pragma unroll
+  for (int i = 0; i < BB_WARPS; ++i) {
+    const int t = red[i];
+    woff += i < warp ? t : 0;
+    sum += t;
+  }
+  __syncthreads();   // red is reused
+  *total = sum;
+  return woff + incl - v;
+}
+
+template <bool NUM, int BB_THREADS>
+__global__ void __launch_bounds__(BB_THREADS)
+k_block_staged(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int ucap, int* __restrict__ rp,
+               int* __restrict__ C_col, double* __restrict__ C_val, Counters* __restrict__ ctr,
+               const int* __restrict__ count_dev) {
+  if (count_dev) count = *count_dev;   // the row count as the binning pass left it on the device
+  if ((int)blockIdx.x >= count) return;   // no row for this block (uniform)
+  constexpr int BB_WARPS = BB_THREADS / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = bb_words(B.cols);
+  const StagedSmem L(W, ucap, NUM, BB_THREADS);
+  double* sums = reinterpret_cast<double*>(smem + L.sums);      // [ucap]
+  double* prod = reinterpret_cast<double*>(smem + L.prod);      // [ucap]
+  int* ocol = reinterpret_cast<int*>(smem + L.ocol);            // [ucap] window column of entry k
+  double* s_a = reinterpret_cast<double*>(smem + L.sa);         // [BB_THREADS]
+  int* scol = reinterpret_cast<int*>(smem + L.scol);            // [ucap]
+  unsigned* bits = reinterpret_cast<unsigned*>(smem + L.bits);  // [W]
+  int* s_start = reinterpret_cast<int*>(smem + L.start);        // [BB_THREADS] an entry's first product
+  int* s_src = reinterpret_cast<int*>(smem + L.src);            // [BB_THREADS] B index of product p, less p
+  int* red = reinterpret_cast<int*>(smem + L.red);
+  unsigned short* rank = reinterpret_cast<unsigned short*>(smem + L.rank);   // [W]
+  const int tid = threadIdx.x;
+  const bool one_window = B.cols <= BB_WINDOW;
+  const int win = one_window ? 32 * W : BB_WIDE_WINDOW;
+  for (int w = tid; w < W; w += BB_THREADS) bits[w] = 0u;
+  __syncthreads();
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int r = list[idx];
+    const int a0 = __ldg(A.rp + r), a1 = __ldg(A.rp + r + 1);
+    int g0 = 0, g1 = 0;
+    if (NUM) { g0 = __ldg(rp + r); g1 = __ldg(rp + r + 1); }
+    // 1. stage the products, BB_THREADS entries of A at a time
+    int u = 0, mn = INT_MAX, mx = INT_MIN;
+    bool bad = false, full = false;
+    for (int e0 = a0; e0 < a1; e0 += BB_THREADS) {   // block-uniform
+      const int e = e0 + tid;
+      int len = 0, src = 0;
+      if (e < a1) {
+        const int j = __ldg(A.col + e);
+        src = __ldg(B.rp + j);
+        len = __ldg(B.rp + j + 1) - src;
+        if (NUM) s_a[tid] = __ldg(A.val + e);
+      }
+      int chunk;
+      const int off = bb_excl_scan<BB_WARPS>(len, red, &chunk);
+      if (u + chunk > ucap) { full = true; break; }   // block-uniform; not within the class limit
+      s_start[tid] = off;   // entries past the row start at `chunk`, above every product
+      s_src[tid] = src - off;
+      __syncthreads();
+#pragma unroll 4
+      for (int p = tid; p < chunk; p += BB_THREADS) {
+        int i = 0;   // the last entry that starts at or before p
+#pragma unroll
+        for (int step = BB_THREADS / 2; step > 0; step >>= 1)
+          if (s_start[i + step] <= p) i += step;
+        const int q = s_src[i] + p;
+        const int c = __ldg(B.col + q);
+        scol[u + p] = c;
+        if (NUM) prod[u + p] = __dmul_rn(s_a[i], __ldg(B.val + q));
+        if ((unsigned)c >= (unsigned)B.cols) bad = true;
+        else { mn = min(mn, c); mx = max(mx, c); }
+      }
+      u += chunk;
+      __syncthreads();   // the entry tables are rewritten by the next chunk
+    }
+    if (full && tid == 0) atomicOr(&ctr->status, ST_TABLE_FULL);
+    bb_minmax<BB_WARPS>(mn, mx, red);
+    int lo = (mn == INT_MAX || full) ? INT_MAX : (one_window ? 0 : mn);
+    int done = 0;   // entries of the row in the windows before this one
+    while (lo != INT_MAX) {   // block-uniform
+      const long long hi = (long long)lo + win;   // window [lo, hi)
+      // 2. mark
+      int wmax = INT_MIN, next = INT_MAX;
+      for (int p = tid; p < u; p += BB_THREADS) {
+        const int c = scol[p];
+        if ((unsigned)c >= (unsigned)B.cols || c < lo) continue;
+        if (c >= hi) { next = min(next, c); continue; }
+        const int d = c - lo;
+        atomicOr(&bits[d >> 5], 1u << (d & 31));
+        wmax = max(wmax, d);
+      }
+      bb_minmax<BB_WARPS>(next, wmax, red);
+      const int nw = wmax >= 0 ? (wmax >> 5) + 1 : 0;   // words holding the window's columns
+      // 3. rank: thread t owns the cw words from t * cw (cw odd: the lanes of a warp on 32 banks)
+      const int cw = ((nw + BB_THREADS - 1) / BB_THREADS) | 1;
+      const int w0 = min(nw, tid * cw), w1 = min(nw, w0 + cw);
+      int pc = 0;
+      for (int w = w0; w < w1; ++w) pc += __popc(bits[w]);
+      int total;
+      int run = bb_excl_scan<BB_WARPS>(pc, red, &total);
+      if (NUM) {
+        for (int w = w0; w < w1; ++w) {
+          rank[w] = (unsigned short)run;
+          run += __popc(bits[w]);
+        }
+        for (int i = tid; i < total; i += BB_THREADS) sums[i] = 0.0;
+        __syncthreads();
+        // 4. sums (products rounded on their own, added in no fixed order); every product of an
+        //    entry records the entry's window column
+        for (int p = tid; p < u; p += BB_THREADS) {
+          const int c = scol[p];
+          if ((unsigned)c >= (unsigned)B.cols || c < lo || c >= hi) continue;
+          const int d = c - lo;
+          const int w = d >> 5;
+          const int k = rank[w] + __popc(bits[w] & ((1u << (d & 31)) - 1u));
+          ocol[k] = d;
+          atomicAdd(&sums[k], prod[p]);
+        }
+        __syncthreads();
+        // 5. write entry by entry, consecutive threads on consecutive entries; clear the words
+        for (int k = tid; k < total; k += BB_THREADS) {
+          const int d = ocol[k];
+          const int o = done + k;
+          if (o < g1 - g0) {
+            C_col[g0 + o] = lo + d;
+            C_val[g0 + o] = sums[k];
+          }
+          bits[d >> 5] = 0u;
+        }
+      } else {
+        for (int w = w0; w < w1; ++w) bits[w] = 0u;   // after the scan: every popcount is taken
+      }
+      done += total;
+      __syncthreads();
+      lo = next;
+    }
+    if (bad) atomicOr(&ctr->status, ST_INVALID);
+    if (tid == 0 && !full) {
+      if (!NUM) rp[r] = done;
+      else if (g1 - g0 != done) atomicOr(&ctr->status, ST_MISMATCH);
+    }
+  }
+}
+
+template <bool NUM, int THREADS>
+static void launch_block_staged_t(const DevCsr& A, const DevCsr& B, const int* list, int count, int ucap, int* rp,
+                                  int* C_col, double* C_val, Counters* ctr, cudaStream_t s, const int* count_dev) {
+  const size_t bytes = StagedSmem(bb_words(B.cols), ucap, NUM, THREADS).bytes;
+  auto kern = k_block_staged<NUM, THREADS>;
+  const int per_sm = blocks_per_sm((const void*)kern, THREADS, bytes);
+  const int blocks = std::max(1, std::min(count, num_sms() * std::max(per_sm, 1)));
+  kern<<<blocks, THREADS, bytes, s>>>(A, B, list, count, ucap, rp, C_col, C_val, ctr, count_dev);
+}
+
 template <bool NUM, int THREADS>
 static void launch_block_bitvec_t(const DevCsr& A, const DevCsr& B, const int* list, int count, int sums_cap, int* rp,
                                   int* C_col, double* C_val, Counters* ctr, cudaStream_t s, const int* count_dev) {
@@ -604,14 +806,14 @@ static void launch_block_bitvec_t(const DevCsr& A, const DevCsr& B, const int* l
 }
 
 // The block takes about eight products per thread: 128 threads for rows of up to 1024 products,
-// 256 up to 2048, 512 beyond (umax: the longest row of the launch).
+// 256 up to 2048 (both staged), 512 beyond (umax: the longest row of the launch).
 template <bool NUM>
 static void launch_block_bitvec(const DevCsr& A, const DevCsr& B, const int* list, int count, int umax, int* rp,
                                 int* C_col, double* C_val, Counters* ctr, cudaStream_t s, const int* count_dev) {
   if (count <= 0) return;
   const int sums_cap = std::max(1, std::min(umax, BB_MAX_U));
-  if (umax <= 1024) launch_block_bitvec_t<NUM, 128>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
-  else if (umax <= 2048) launch_block_bitvec_t<NUM, 256>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
+  if (umax <= 1024) launch_block_staged_t<NUM, 128>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
+  else if (umax <= BB_STAGE_U) launch_block_staged_t<NUM, 256>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
   else launch_block_bitvec_t<NUM, 512>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
 }
 

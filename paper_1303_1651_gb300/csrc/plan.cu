@@ -72,7 +72,7 @@ k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l
   const int lane = threadIdx.x & 31;
   const long long G = (long long)gridDim.x * BIN_THREADS;
   long long F = 0, umax = 0;
-  int umax_merge = 0, umax_w = 0, cnt[NUM_CLS] = {0, 0, 0, 0, 0};
+  int umax_merge = 0, umax_w = 0, umax_b = 0, cnt[NUM_CLS] = {0, 0, 0, 0, 0};
   bool bad = false;
   // the loop bound is warp-uniform (the warp's first row) so the ballots below see every lane
   for (long long wb = (long long)blockIdx.x * BIN_THREADS + (threadIdx.x & ~31); wb < A.rows; wb += G * BIN_ROWS) {
@@ -125,6 +125,7 @@ k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l
         umax = max(umax, u);
         if (c == CLS_M1 || c == CLS_M2) umax_merge = max(umax_merge, (int)u);
         if (c == CLS_W) umax_w = max(umax_w, (int)u);
+        if (c == CLS_B) umax_b = max(umax_b, (int)u);
       }
       // listed classes (the rare long rows): warp-aggregated appends; the others are only counted
 #pragma unroll
@@ -146,7 +147,7 @@ k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l
   }
   // block totals, then one global atomic of each per block
   __shared__ long long s_F[BIN_THREADS / 32], s_umax[BIN_THREADS / 32];
-  __shared__ int s_um[BIN_THREADS / 32], s_uw[BIN_THREADS / 32], s_cnt[BIN_THREADS / 32][NUM_CLS];
+  __shared__ int s_um[BIN_THREADS / 32], s_uw[BIN_THREADS / 32], s_ub[BIN_THREADS / 32], s_cnt[BIN_THREADS / 32][NUM_CLS];
   const int w = threadIdx.x >> 5;
   const long long wF = warp_sum_ll(F);
   long long wm = umax;
@@ -154,25 +155,27 @@ k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l
   for (int d = 16; d > 0; d >>= 1) wm = max(wm, __shfl_xor_sync(FULL, wm, d));
   const int wum = __reduce_max_sync(FULL, umax_merge);
   const int wuw = __reduce_max_sync(FULL, umax_w);
+  const int wub = __reduce_max_sync(FULL, umax_b);
   int wc[NUM_CLS];
 #pragma unroll
   for (int cc = 0; cc < NUM_CLS; ++cc) wc[cc] = __reduce_add_sync(FULL, cnt[cc]);
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(&ctr->status, ST_INVALID);
   if (lane == 0) {
-    s_F[w] = wF; s_umax[w] = wm; s_um[w] = wum; s_uw[w] = wuw;
+    s_F[w] = wF; s_umax[w] = wm; s_um[w] = wum; s_uw[w] = wuw; s_ub[w] = wub;
 #pragma unroll
     for (int cc = 0; cc < NUM_CLS; ++cc) s_cnt[w][cc] = wc[cc];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     long long t = 0, mx = 0;
-    int mm = 0, mw = 0;
+    int mm = 0, mw = 0, mb = 0;
     for (int i = 0; i < BIN_THREADS / 32; ++i) {
-      t += s_F[i]; mx = max(mx, s_umax[i]); mm = max(mm, s_um[i]); mw = max(mw, s_uw[i]);
+      t += s_F[i]; mx = max(mx, s_umax[i]); mm = max(mm, s_um[i]); mw = max(mw, s_uw[i]); mb = max(mb, s_ub[i]);
     }
     if (t) atomicAdd(&ctr->F, (unsigned long long)t);
     if (mm > 0) atomicMax(&ctr->max_u_merge, mm);
     if (mw > 0) atomicMax(&ctr->max_u_w, mw);
+    if (mb > 0) atomicMax(&ctr->max_u_b, mb);
     if (mx > INT_MAX) { atomicOr(&ctr->status, ST_OVERFLOW); mx = INT_MAX; }
     if (mx > 0) atomicMax(&ctr->max_u, (int)mx);
   }
