@@ -261,7 +261,10 @@ spgemm_status_t spgemm_multiply(const spgemm_csr_t* A, const spgemm_csr_t* B, co
  * them.  Nothing the call enqueues depends on the data on the host side (every class kernel reads
  * its row count on the device), so the call can be captured into a CUDA graph once (after one
  * eager call, which sets the kernels' attributes) and the graph replayed for new contents of the
- * same arrays: a product of the same shapes per replay, with one read-back.  Errors: INVALID,
+ * same arrays: a product of the same shapes per replay, with one read-back.  The class kernels
+ * that do not depend on one another run on two internal streams, forked from and joined back to
+ * stream by events within the call (a captured graph holds them side by side); the streams and
+ * events are created on the calling thread's first call on a device and kept until it ends.  Errors: INVALID,
  * ALLOC, CUDA (host checks and launches; device errors are reported by spgemm_multiply_result). */
 spgemm_status_t spgemm_multiply_async(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
                                       void* workspace, size_t workspace_bytes, int32_t* C_row_ptr, int32_t* C_col,

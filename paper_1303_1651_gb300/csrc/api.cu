@@ -2,6 +2,7 @@
 // See include/spgemm_gb300.h for the contract of every entry point.
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -100,6 +101,7 @@ bool desc_ok(const spgemm_csr_t* M, bool csc = false) {
   if (!M || M->rows < 0 || M->cols < 0 || M->nnz < 0 || M->nnz > INT32_MAX) return false;
   if (!M->row_ptr && (csc ? M->cols : M->rows) > 0) return false;
   if (!M->col_idx && M->nnz > 0) return false;
+  if (M->nnz > 0 && (M->rows == 0 || M->cols == 0)) return false;   // entries need a row and a column
   return true;
 }
 
@@ -278,8 +280,10 @@ static spgemm_status_t plan_args(const spgemm_csr_t* A, const spgemm_csr_t* B, c
 
 // Enqueue the plan's device work (conversion of operands given by columns, optional validation,
 // binning) on s; the counters stay on the device.
+// zero_fused: the binning kernel also clears the single-pass product's tile states.
 static void plan_enqueue(spgemm_plan_s* p, const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_options_t* opt,
-                         void* workspace, const bool csc[2], int nslabs, const Layout& L, cudaStream_t s) {
+                         void* workspace, const bool csc[2], int nslabs, const Layout& L, cudaStream_t s,
+                         bool zero_fused = false) {
   p->A = to_dev(*A);
   p->B = to_dev(*B);
   p->lim = limits_from(opt);
@@ -323,7 +327,9 @@ static void plan_enqueue(spgemm_plan_s* p, const spgemm_csr_t* A, const spgemm_c
   }
   int* lists[NUM_CLS] = {nullptr, nullptr, (int*)(p->ws + L.list_w), (int*)(p->ws + L.list_b),
                          (int*)(p->ws + L.list_g)};
-  launch_bin(p->A, p->B, p->lim, p->ws + L.cls, lists, p->ctr, s);
+  launch_bin(p->A, p->B, p->lim, p->ws + L.cls, lists, p->ctr, s,
+             zero_fused ? (unsigned long long*)(p->ws + L.fused) : nullptr,
+             (long long)(fused_tile_state_bytes(p->A.rows) / sizeof(unsigned long long)));
 }
 
 spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spgemm_csr_t* B,
@@ -359,12 +365,62 @@ spgemm_status_t spgemm_plan(spgemm_plan_t* out, const spgemm_csr_t* A, const spg
 // row count on the device (a class with no rows costs an empty launch), the dense slabs are cleared
 // by their kernel, and both tile forms of the fused pass are launched (the one the binning did not
 // choose returns at once).  The counters are read back once, at the end.
+// Side streams and events of spgemm_multiply_async, one set per host thread and device (calls from
+// several threads never share an event).  The class kernels that do not depend on one another (the
+// three structure passes, the two tile forms, the three value passes) go to separate streams joined
+// by events, so a CUDA graph captured from the call holds them side by side instead of in a chain.
+// Created on the thread's first call on a device and kept until the thread ends.
+struct ForkSet {
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool ok = false;
+  ForkSet() = default;
+  ForkSet(const ForkSet&) = delete;
+  ForkSet& operator=(const ForkSet&) = delete;
+  ~ForkSet() {
+    for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);
+    for (cudaStream_t t : side) if (t) cudaStreamDestroy(t);
+  }
+};
+
+static ForkSet* fork_set() {
+  thread_local std::map<int, ForkSet> sets;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  ForkSet& f = sets[dev];
+  if (!f.ok) {
+    bool good = true;
+    for (cudaStream_t& t : f.side)
+      if (!t) good = good && cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t& e : f.ev)
+      if (!e) good = good && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    f.ok = good;
+    if (!good) return nullptr;   // the call then runs on one stream
+  }
+  return &f;
+}
+
+// n side streams wait for the work enqueued on s so far (fork), or s waits for them (join).
+static void fork_to(ForkSet* f, int n, cudaStream_t s) {
+  if (!f) return;
+  cudaEventRecord(f->ev[0], s);
+  for (int i = 0; i < n; ++i) cudaStreamWaitEvent(f->side[i], f->ev[0], 0);
+}
+static void join_from(ForkSet* f, int n, cudaStream_t s) {
+  if (!f) return;
+  for (int i = 0; i < n; ++i) {
+    cudaEventRecord(f->ev[1 + i], f->side[i]);
+    cudaStreamWaitEvent(s, f->ev[1 + i], 0);
+  }
+}
+
 // Enqueue spgemm_multiply's work on s (p: a plan object on the caller's stack, holding no pinned
-// slot unless the caller gave it one).  Host checks only; nothing is read back.
+// slot unless the caller gave it one).  Host checks only; nothing is read back.  fork: independent
+// class kernels on side streams (above).
 static spgemm_status_t multiply_enqueue(spgemm_plan_s& p, const spgemm_csr_t* A, const spgemm_csr_t* B,
                                         const spgemm_options_t* opt, void* workspace, size_t workspace_bytes,
                                         int32_t* C_row_ptr, int32_t* C_col, double* C_val, int64_t capacity,
-                                        cudaStream_t s) {
+                                        cudaStream_t s, bool fork = false) {
   if (!C_row_ptr || capacity < 0) return SPGEMM_ERR_INVALID;
   if ((!C_col || !C_val) && capacity > 0) return SPGEMM_ERR_INVALID;
   bool csc[2];
@@ -374,33 +430,41 @@ static spgemm_status_t multiply_enqueue(spgemm_plan_s& p, const spgemm_csr_t* A,
   if (a != SPGEMM_OK) return a;
   if ((!A->val && A->nnz > 0) || (!B->val && B->nnz > 0)) return SPGEMM_ERR_INVALID;
   if (fault_is("nnz_overflow")) capacity = 0;
-  plan_enqueue(&p, A, B, opt, workspace, csc, nslabs, L, s);
+  // the fused pass's tile states and ticket are cleared by the binning kernel (after any
+  // conversion of an operand given by columns, whose scan takes tickets too)
+  plan_enqueue(&p, A, B, opt, workspace, csc, nslabs, L, s, true);
   const int m = p.A.rows;
   if (m == 0) {
     cudaMemsetAsync(C_row_ptr, 0, sizeof(int32_t), s);
   } else {
     DevCsr Av, Bv;
     prepare_values(&p, A->val, B->val, Av, Bv, s);
-    cudaMemsetAsync(&p.ctr->ticket, 0, sizeof(unsigned), s);
-    cudaMemsetAsync(p.ws + L.fused, 0, fused_tile_state_bytes(m), s);
+    ForkSet* f = fork ? fork_set() : nullptr;
+    cudaStream_t s1 = f ? f->side[0] : s, s2 = f ? f->side[1] : s;
     const int* cnt_dev = p.ctr->count;
     const int* lw = (const int*)(p.ws + L.list_w);
     const int* lb = (const int*)(p.ws + L.list_b);
     const int* lg = (const int*)(p.ws + L.list_g);
     const Limits& lim = p.lim;
+    fork_to(f, 2, s);
     if (lim.warp_u > 0)
       launch_hash_symbolic(CLS_W, Av, Bv, lw, m, C_row_ptr, p.ctr, s, lim.warp_u, p.wopt, cnt_dev + CLS_W);
-    if (lim.block_u > 0) launch_hash_symbolic(CLS_B, Av, Bv, lb, m, C_row_ptr, p.ctr, s, lim.block_u, p.wopt, cnt_dev + CLS_B);
-    launch_dense_symbolic(Av, Bv, lg, m, p.ws + L.slabs, p.nslabs, C_row_ptr, p.ctr, s, cnt_dev + CLS_G, true);
+    if (lim.block_u > 0) launch_hash_symbolic(CLS_B, Av, Bv, lb, m, C_row_ptr, p.ctr, s1, lim.block_u, p.wopt, cnt_dev + CLS_B);
+    launch_dense_symbolic(Av, Bv, lg, m, p.ws + L.slabs, p.nslabs, C_row_ptr, p.ctr, s2, cnt_dev + CLS_G, true);
+    join_from(f, 2, s);
+    fork_to(f, 1, s);
     for (int wide = 0; wide < 2; ++wide)
       launch_merge_fused(wide, p.values_mode, Av, Bv, p.ws + L.cls, C_row_ptr, C_col, C_val, capacity,
-                         (unsigned long long*)(p.ws + L.fused), p.ctr, s, p.spin_limit, p.drop_tile,
+                         (unsigned long long*)(p.ws + L.fused), p.ctr, wide ? s1 : s, p.spin_limit, p.drop_tile,
                          &p.ctr->max_u_merge);
+    join_from(f, 1, s);
+    fork_to(f, 2, s);
     if (lim.warp_u > 0)
       launch_hash_numeric(CLS_W, Av, Bv, lw, m, C_row_ptr, C_col, C_val, p.ctr, s, lim.warp_u, p.wopt, cnt_dev + CLS_W);
     if (lim.block_u > 0)
-      launch_hash_numeric(CLS_B, Av, Bv, lb, m, C_row_ptr, C_col, C_val, p.ctr, s, lim.block_u, p.wopt, cnt_dev + CLS_B);
-    launch_dense_numeric(Av, Bv, lg, m, p.ws + L.slabs, p.nslabs, C_row_ptr, C_col, C_val, p.ctr, s, cnt_dev + CLS_G);
+      launch_hash_numeric(CLS_B, Av, Bv, lb, m, C_row_ptr, C_col, C_val, p.ctr, s1, lim.block_u, p.wopt, cnt_dev + CLS_B);
+    launch_dense_numeric(Av, Bv, lg, m, p.ws + L.slabs, p.nslabs, C_row_ptr, C_col, C_val, p.ctr, s2, cnt_dev + CLS_G);
+    join_from(f, 2, s);
   }
   return cudaGetLastError() == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
@@ -426,7 +490,7 @@ spgemm_status_t spgemm_multiply_async(const spgemm_csr_t* A, const spgemm_csr_t*
                                       double* C_val, int64_t capacity, void* stream) {
   spgemm_plan_s p;
   return multiply_enqueue(p, A, B, opt, workspace, workspace_bytes, C_row_ptr, C_col, C_val, capacity,
-                          (cudaStream_t)stream);
+                          (cudaStream_t)stream, true);
 }
 
 spgemm_status_t spgemm_multiply_result(const void* workspace, int64_t* nnz_c, int64_t* products, void* stream) {

@@ -57,11 +57,21 @@ k_grad_a(DevCsr A, DevCsr B, const int* __restrict__ C_rp, const int* __restrict
   if (__any_sync(FULL, miss) && (threadIdx.x & 31) == 0) atomicOr(&ctr->status, ST_MISMATCH);
 }
 
-// Transposed structure of A: T_cp (A.cols + 1), T_row (nnzA), T_src (nnzA: position in A).
-__global__ void k_count_cols(DevCsr A, int* __restrict__ cnt) {
+// Transposed structure of A: T_cp (A.cols + 1), T_row (nnzA), T_src (nnzA: position in A).  The
+// operand may come straight from the caller, before any validation: an index outside [0, A.cols)
+// is counted in the last column, so every entry of T_row and T_src is still written (nothing is
+// addressed out of range), and the status reports SPGEMM_ERR_INVALID.
+__device__ __forceinline__ int clamp_col(int j, int ncols) { return j < 0 ? 0 : (j >= ncols ? ncols - 1 : j); }
+
+__global__ void k_count_cols(DevCsr A, int* __restrict__ cnt, Counters* __restrict__ ctr) {
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < A.nnz; p += stride)
-    atomicAdd(&cnt[__ldg(A.col + p)], 1);
+  bool bad = false;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < A.nnz; p += stride) {
+    const int j = __ldg(A.col + p);
+    bad = bad || (unsigned)j >= (unsigned)A.cols;
+    atomicAdd(&cnt[clamp_col(j, A.cols)], 1);
+  }
+  if (bad) atomicOr(&ctr->status, ST_INVALID);
 }
 
 __global__ void k_scatter_cols(DevCsr A, const int* __restrict__ T_cp, int* __restrict__ next,
@@ -69,7 +79,7 @@ __global__ void k_scatter_cols(DevCsr A, const int* __restrict__ T_cp, int* __re
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long pl = (long long)blockIdx.x * blockDim.x + threadIdx.x; pl < A.nnz; pl += stride) {
     const int p = (int)pl;
-    const int j = __ldg(A.col + p);
+    const int j = clamp_col(__ldg(A.col + p), A.cols);   // as counted by k_count_cols
     const int d = __ldg(T_cp + j) + atomicAdd(&next[j], 1);
     T_row[d] = row_of(A.rp, A.rows, p);
     T_src[d] = p;
@@ -149,12 +159,13 @@ void launch_transpose(const DevCsr& A, void* ws, Counters* ctr, cudaStream_t s) 
   cudaMemsetAsync(T_cp, 0, 4 * ((size_t)A.cols + 1), s);
   cudaMemsetAsync(next, 0, 4 * (size_t)std::max(A.cols, 1), s);
   const int grid = num_sms() * 8;
-  if (A.nnz > 0) k_count_cols<<<grid, 256, 0, s>>>(A, T_cp);
+  // (a matrix with entries but no columns has no column to count them in: the plan rejects it)
+  if (A.nnz > 0 && A.cols > 0) k_count_cols<<<grid, 256, 0, s>>>(A, T_cp, ctr);
   // counts sit in T_cp[0..cols-1]; the scan turns them into column pointers
   cudaMemsetAsync(&ctr->ticket, 0, sizeof(unsigned), s);
   cudaMemsetAsync(scan_state, 0, scan_tile_state_bytes((long long)A.cols + 1), s);
   launch_scan(T_cp, (long long)A.cols + 1, scan_state, ctr, nullptr, s);
-  if (A.nnz > 0) {
+  if (A.nnz > 0 && A.cols > 0) {
     k_scatter_cols<<<grid, 256, 0, s>>>(A, T_cp, next, T_row, T_src);
     k_sort_cols<<<std::max(1, std::min(grid, (A.cols + 255) / 256)), 256, 0, s>>>(A.cols, T_cp, T_row, T_src);
   }
@@ -185,15 +196,19 @@ void launch_grad_b(const DevCsr& A, const DevCsr& B, const void* tws, const int*
 __global__ void k_gather(const int* __restrict__ perm, const double* __restrict__ src, double* __restrict__ dst,
                          long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x; d < n; d += stride)
-    dst[d] = __ldg(src + __ldg(perm + d));
+  for (long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x; d < n; d += stride) {
+    const int q = __ldg(perm + d);
+    dst[d] = (unsigned long long)(unsigned)q < (unsigned long long)n ? __ldg(src + q) : 0.0;   // in range
+  }
 }
 
 __global__ void k_scatter(const int* __restrict__ perm, const double* __restrict__ src, double* __restrict__ dst,
                           long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x; d < n; d += stride)
-    dst[__ldg(perm + d)] = __ldg(src + d);
+  for (long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x; d < n; d += stride) {
+    const int q = __ldg(perm + d);
+    if ((unsigned long long)(unsigned)q < (unsigned long long)n) dst[q] = __ldg(src + d);   // in range
+  }
 }
 
 void launch_gather(const int* perm, const double* src, double* dst, long long n, cudaStream_t s) {

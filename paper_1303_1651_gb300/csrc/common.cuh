@@ -18,7 +18,8 @@ enum RowClass : uint8_t {
   CLS_W = 2,    // warp per row: bit vector, register sort or hash table in shared memory
   CLS_B = 3,    // block-per-row shared-memory hash
   CLS_G = 4,    // dense accumulator in global memory over [min, max] (MinMax)
-  NUM_CLS = 5
+  NUM_CLS = 5,
+  CLS_NONE = 255   // a row with an invalid entry: no class kernel reads it (the status says INVALID)
 };
 
 // Status bits (sticky, read by the host after a synchronising call).

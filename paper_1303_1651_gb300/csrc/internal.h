@@ -7,8 +7,10 @@
 namespace spg {
 
 // a1: per-row product counts, row classes, class lists, F, max row count (binning).
+// zero / nzero: when given, the kernel also clears nzero 64-bit words there (the single-pass
+// product's tile states) and the counters' ticket, so that no separate memset precedes that pass.
 void launch_bin(const DevCsr& A, const DevCsr& B, const Limits& lim, uint8_t* cls, int* const lists[NUM_CLS],
-                Counters* ctr, cudaStream_t s);
+                Counters* ctr, cudaStream_t s, unsigned long long* zero = nullptr, long long nzero = 0);
 
 // a3: exclusive scan, in place, of counts[0..n-2] into row_ptr[0..n-1] (n = rows + 1).
 size_t scan_tile_state_bytes(long long n);

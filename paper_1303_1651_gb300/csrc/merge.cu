@@ -252,7 +252,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& g, int tile, unsigne
   int a0 = 0, k = 0;
   if (mine) { a0 = __ldg(A.rp + r); k = __ldg(A.rp + r + 1) - a0; }
   int other = 0;    // FUSED: entry count of a row of another class (from its symbolic pass)
-  if (MODE == MODE_FUSED && inrange && !mine) other = g.rp[r];
+  if (MODE == MODE_FUSED && inrange && !mine && c != CLS_NONE) other = g.rp[r];   // a row without class stays empty
   int gbeg = 0, gend = 0;   // NUM: C's row range
   if (MODE == MODE_NUM && mine) { gbeg = __ldg(g.rp + r); gend = __ldg(g.rp + r + 1); }
   int jcol[MERGE_K];
@@ -636,7 +636,7 @@ __device__ __forceinline__ void merge_tile_pair(const MergeArgs& g, int tile, un
   int a0 = 0, k = 0;
   if (mine) { a0 = __ldg(A.rp + r); k = __ldg(A.rp + r + 1) - a0; }
   int other = 0;
-  if (MODE == MODE_FUSED && inrange && !mine && h == 0) other = g.rp[r];
+  if (MODE == MODE_FUSED && inrange && !mine && c != CLS_NONE && h == 0) other = g.rp[r];
   int gbeg = 0, gend = 0;
   if (MODE == MODE_NUM && mine) { gbeg = __ldg(g.rp + r); gend = __ldg(g.rp + r + 1); }
   int jcol[MERGE_K];

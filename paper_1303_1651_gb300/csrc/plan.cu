@@ -67,10 +67,14 @@ __device__ __noinline__ long long bin_tail(const DevCsr A, const DevCsr B, int p
 // and adds them to the global counters once per block at the end.
 __global__ void __launch_bounds__(BIN_THREADS)
 k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l1, int* l2, int* l3, int* l4,
-      Counters* __restrict__ ctr) {
+      Counters* __restrict__ ctr, unsigned long long* __restrict__ zero, long long nzero) {
   int* lists[NUM_CLS] = {l0, l1, l2, l3, l4};
   const int lane = threadIdx.x & 31;
   const long long G = (long long)gridDim.x * BIN_THREADS;
+  if (zero) {   // the single-pass product's tile states, and its ticket (a conversion's scan used it)
+    for (long long i = (long long)blockIdx.x * BIN_THREADS + threadIdx.x; i < nzero; i += G) zero[i] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->ticket = 0u;
+  }
   long long F = 0, umax = 0;
   int umax_merge = 0, umax_w = 0, umax_b = 0, cnt[NUM_CLS] = {0, 0, 0, 0, 0};
   bool bad = false;
@@ -96,25 +100,29 @@ k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l
       for (int i = 0; i < BIN_EPR; ++i) {
         len[q][i] = 0;
         if (a0[q] + i < a1[q]) {
-          if ((unsigned)j[q][i] >= (unsigned)B.rows) bad = true;   // also a negative column
+          if ((unsigned)j[q][i] >= (unsigned)B.rows) len[q][i] = -1;   // also a negative column
           else len[q][i] = __ldg(B.rp + j[q][i] + 1) - __ldg(B.rp + j[q][i]);
         }
       }
 #pragma unroll
     for (int q = 0; q < BIN_ROWS; ++q) {
       long long u = 0;
+      bool rowbad = false;   // an entry of A outside B's rows, or a decreasing row pointer
 #pragma unroll
       for (int i = 0; i < BIN_EPR; ++i) {
-        if (len[q][i] < 0) bad = true; else u += len[q][i];
+        if (len[q][i] < 0) rowbad = true; else u += len[q][i];
       }
       if (a1[q] - a0[q] > BIN_EPR) {
         const long long t = bin_tail(A, B, a0[q] + BIN_EPR, a1[q]);
-        if (t < 0) bad = true; else u += t;
+        if (t < 0) rowbad = true; else u += t;
       }
       int c = -1;
-      if (r[q] >= 0) {
+      if (r[q] >= 0 && (rowbad || a1[q] < a0[q])) {
+        // no class: the class kernels would address B's row pointer with the invalid entry
+        bad = true;
+        cls[r[q]] = (uint8_t)CLS_NONE;
+      } else if (r[q] >= 0) {
         const int k = a1[q] - a0[q];
-        if (k < 0) bad = true;
         if (k <= lim.merge_k && u <= lim.m1_u) c = CLS_M1;
         else if (k <= lim.merge_k && u <= lim.m2_u) c = CLS_M2;
         else if (u <= lim.warp_u) c = CLS_W;
@@ -187,14 +195,15 @@ k_bin(DevCsr A, DevCsr B, Limits lim, uint8_t* __restrict__ cls, int* l0, int* l
 }
 
 void launch_bin(const DevCsr& A, const DevCsr& B, const Limits& lim_in, uint8_t* cls, int* const lists[NUM_CLS],
-                Counters* ctr, cudaStream_t s) {
+                Counters* ctr, cudaStream_t s, unsigned long long* zero, long long nzero) {
   if (A.rows <= 0) return;
   Limits lim = lim_in;
   if (B.cols > merge_max_cols()) { lim.m1_u = -1; lim.m2_u = -1; }   // sort keys hold column << log2(N)
   const int per_sm = blocks_per_sm((const void*)k_bin, BIN_THREADS, 0);
   const long long need = ((long long)A.rows + (long long)BIN_THREADS * BIN_ROWS - 1) / ((long long)BIN_THREADS * BIN_ROWS);
   const int grid = (int)std::max(1LL, std::min(need, (long long)num_sms() * per_sm));
-  k_bin<<<grid, BIN_THREADS, 0, s>>>(A, B, lim, cls, lists[0], lists[1], lists[2], lists[3], lists[4], ctr);
+  k_bin<<<grid, BIN_THREADS, 0, s>>>(A, B, lim, cls, lists[0], lists[1], lists[2], lists[3], lists[4], ctr, zero,
+                                     zero ? nzero : 0);
 }
 
 // ---------------------------------------------------------------------------
