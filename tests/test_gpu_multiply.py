@@ -166,3 +166,22 @@ def test_graph_replay_overflow_report():
     with pytest.raises(binding.SpgemmError, match="OVERFLOW"):
         g.run()
     assert g.run(raise_on_overflow=False) == (R["nnz"], R["F"])
+
+
+def test_invalid_entry_reported_without_fault():
+    # a column of A outside B's rows: the binning pass gives its row no class, so no kernel of the
+    # one-call product addresses B's row pointer with it; the call reports INVALID, and the device
+    # is exact on the next product
+    A, B = synth.random_k(2000, 5, 551), synth.random_k(2000, 5, 552)
+    bad = synth.CSR(A.rows, A.cols, A.row_ptr.copy(), A.col_idx.copy(), A.val.copy())
+    bad.col_idx[777] = B.rows + 5
+    dA, dB = dev(bad), dev(B)
+    ws = torch.empty(binding.spgemm_workspace_size(dA, dB), dtype=torch.uint8, device="cuda")
+    F = int(oracle.spgemm(A, B)["F"])
+    C_rp = torch.empty(A.rows + 1, dtype=torch.int32, device="cuda")
+    C_col = torch.empty(F, dtype=torch.int32, device="cuda")
+    C_val = torch.empty(F, dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.SpgemmError, match="INVALID"):
+        binding.spgemm_multiply(dA, dB, C_rp, C_col, C_val, ws)
+    torch.cuda.synchronize()
+    compare(once(A, B), oracle.spgemm(A, B))
