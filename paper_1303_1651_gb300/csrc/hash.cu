@@ -607,23 +607,27 @@ k_block_bitvec(DevCsr A, DevCsr B, const int* __restrict__ list, int count, int 
 constexpr int BB_STAGE_U = 2048;
 
 // Shared memory of k_block_staged, in bytes: sums, products and the entries' columns (numeric),
-// a of the chunk's entries (numeric), the products' columns, bits, entry starts, entry sources,
-// reduction slots, ranks (numeric).
+// the products' columns, bits, reduction slots, ranks (numeric).  The entry tables of the staging
+// step (a of the chunk's entries, starts, sources) are only needed before the windows: in the
+// numeric kernel they share the space of the sums and of the entries' columns (36 KB for rows of
+// up to 1024 products and windows of 2^16 columns, six blocks per SM), in the symbolic one they
+// follow the bits.
 struct StagedSmem {
   size_t sums, prod, ocol, sa, scol, bits, start, src, red, rank, bytes;
   __host__ __device__ StagedSmem(int words, int ucap, bool num, int threads) {
+    const size_t u = (size_t)ucap, t = (size_t)threads;
     sums = 0;
-    prod = sums + (num ? 8 * (size_t)ucap : 0);
-    ocol = prod + (num ? 8 * (size_t)ucap : 0);
-    sa = ocol + (num ? 4 * (size_t)ucap : 0);
-    sa = (sa + 7) / 8 * 8;
-    scol = sa + (num ? 8 * (size_t)threads : 0);
-    bits = scol + 4 * (size_t)ucap;
-    start = bits + 4 * (size_t)words;
-    src = start + 4 * (size_t)threads;
-    red = src + 4 * (size_t)threads;
-    rank = red + 4 * 4 * (size_t)(threads / 32);
+    prod = sums + (num ? (8 * u > 8 * t ? 8 * u : 8 * t) : 0);
+    ocol = prod + (num ? 8 * u : 0);
+    scol = ocol + (num ? (4 * u > 8 * t ? 4 * u : 8 * t) : 0);
+    scol = (scol + 7) / 8 * 8;
+    bits = scol + 4 * u;
+    red = bits + 4 * (size_t)words + (num ? 0 : 8 * t);
+    rank = red + 4 * 4 * (t / 32);
     bytes = rank + (num ? 2 * (size_t)words : 0);
+    sa = sums;                                       // numeric only
+    start = num ? ocol : bits + 4 * (size_t)words;
+    src = start + 4 * t;
   }
 };
 
