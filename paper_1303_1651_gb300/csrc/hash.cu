@@ -810,13 +810,16 @@ static void launch_block_bitvec_t(const DevCsr& A, const DevCsr& B, const int* l
 }
 
 // The block takes about eight products per thread: 128 threads for rows of up to 1024 products,
-// 256 up to 2048 (both staged), 512 beyond (umax: the longest row of the launch).
+// 256 up to 2048 (both staged), 512 beyond (umax: the longest row of the launch).  The structure
+// pass of rows of up to 1024 products runs 64 threads a row (about sixteen products each): 24.3 against
+// 25.2 ms for the batched workload, where 32 threads, 256, or 64 for the value pass too were slower.
 template <bool NUM>
 static void launch_block_bitvec(const DevCsr& A, const DevCsr& B, const int* list, int count, int umax, int* rp,
                                 int* C_col, double* C_val, Counters* ctr, cudaStream_t s, const int* count_dev) {
   if (count <= 0) return;
   const int sums_cap = std::max(1, std::min(umax, BB_MAX_U));
-  if (umax <= 1024) launch_block_staged_t<NUM, 128>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
+  if (umax <= 1024 && !NUM) launch_block_staged_t<NUM, 64>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
+  else if (umax <= 1024) launch_block_staged_t<NUM, 128>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
   else if (umax <= BB_STAGE_U) launch_block_staged_t<NUM, 256>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
   else launch_block_bitvec_t<NUM, 512>(A, B, list, count, sums_cap, rp, C_col, C_val, ctr, s, count_dev);
 }
