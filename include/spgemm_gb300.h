@@ -150,7 +150,7 @@ typedef struct {
                              product gives up (0: 2^24).  With a small limit and debug_drop_tile, a
                              test can make the wait run out (SPGEMM_ERR_TIMEOUT) */
   int32_t debug_drop_tile;    /* testing: 0 none; t > 0: placement unit t - 1 of the single-pass product
-                             (groups of 128 rows, or of 64 where some sort-class row has more than 32
+                             (groups of 128 rows, or of 32 where some sort-class row has more than 32
                              products; tiles of 32 rows with merge_values = 2) publishes neither its
                              entry count nor its prefix, so the look-backs
                              that reach it give up after debug_spin_limit rounds.  C is then wrong

@@ -35,7 +35,7 @@ def fused(A, B, opt):
 
 
 @pytest.mark.parametrize("k,form", [(4, {}), (4, dict(merge_values=2)), (8, {})],
-                         ids=["128-row-groups", "32-row-tiles", "64-row-groups"])
+                         ids=["128-row-groups", "32-row-tiles", "32-row-groups"])
 def test_lookback_gives_up_and_the_device_stays_usable(k, form):
     A, B = synth.random_k(20_000, k, 481), synth.random_k(20_000, k, 482)
     err, C_col = fused(A, B, binding.options(debug_drop_tile=1 + 100, debug_spin_limit=512, **form))
