@@ -554,9 +554,9 @@ def run_ours(args, rank, world, local_rank):
         num_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(p["ev0"], p["ev1"])]))
         cls = p["info"]["rows_per_class"]
         wide = p["info"]["max_row_products"] > 32 and cls["M2"] > 0
-        # default options: 32-product tiles use the direct form, 64-product rows the two-lanes-per-row form;
+        # default options: 32-product tiles use the direct form, 64-product rows the four-lanes-per-row form;
         # longer rows add the warp-, block- and dense-class kernels to the same call
-        kern = "k_merge_pair<fused>" if wide else "k_merge<fused,32>"
+        kern = "k_merge_quad<fused>" if wide else "k_merge<fused,32>"
         if any(cls[c] > 0 for c in ("W", "B", "G")):
             kern = "spgemm_compute (" + kern + " + " + ", ".join(c for c in ("W", "B", "G") if cls[c] > 0) + " class kernels)"
         d = {"F": p["info"]["products"], "nnz_c": p["nnz"], "bytes_min": bmin, "compute_ms": num_ms,
