@@ -342,3 +342,38 @@ def test_sort_classes_off_past_limit(fused):
     cls = C["info"]["rows_per_class"]
     assert cls["M1"] + cls["M2"] == 0 and cls["W"] == 1000, cls
     compare(C, oracle.spgemm(A, B), single=True)
+
+
+def _groups_across_lanes(case):
+    """Rows of up to 64 products whose groups of equal columns cross the lanes of the fused pass
+    (four lanes of 16 sorted positions a row): one group of 64, many short groups, groups of 7."""
+    rng = np.random.default_rng(620)
+    n = 3000
+    if case == "one-group-of-64":      # every row of B is one column eight times
+        B = synth.CSR(n, n, (np.arange(n + 1) * 8).astype(np.int32), np.full(n * 8, 5, np.int32),
+                      rng.uniform(-1, 1, n * 8))
+        return synth.random_k(n, 8, 621), B
+    if case == "short-groups":         # rows of B with 6..8 entries over 12 columns
+        lens = rng.integers(6, 9, n)
+        rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+        B = synth.CSR(n, n, rp, rng.integers(0, 12, int(rp[-1])).astype(np.int32), rng.uniform(-1, 1, int(rp[-1])))
+        return synth.random_k(n, 8, 622), B
+    # seven entries of A times identical rows of nine columns: groups of 7 across 16-position edges
+    B = synth.CSR(n, n, (np.arange(n + 1) * 9).astype(np.int32), np.tile(np.arange(100, 109, dtype=np.int32), n),
+                  rng.uniform(-1, 1, n * 9))
+    return synth.random_k(n, 7, 623), B
+
+
+@pytest.mark.parametrize("case", ["one-group-of-64", "short-groups", "groups-of-7"])
+def test_groups_across_lanes_bit_identical(case):
+    # the single pass (four lanes a row) and the three-call path (two lanes a row) sum every group
+    # in the same order: C is bit-identical between them, and equal to the oracle
+    A, B = _groups_across_lanes(case)
+    R = oracle.spgemm(A, B)
+    fused = gpu_product(A, B, fused=True)
+    three = gpu_product(A, B)
+    assert fused["info"]["rows_per_class"]["M2"] > 0
+    compare(fused, R, single=True)
+    for k in ("row_ptr", "col_idx"):
+        assert np.array_equal(np.asarray(fused[k], np.int64), np.asarray(three[k], np.int64))
+    assert np.array_equal(np.asarray(fused["val"]).view(np.int64), np.asarray(three["val"]).view(np.int64))
