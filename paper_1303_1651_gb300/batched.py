@@ -166,3 +166,40 @@ class PerMatrix:
             finally:
                 binding.spgemm_free(plan)
         self.F = F
+
+
+def main(argv=None):
+    """Replay the batch of `synth.batch_problems` as one block-diagonal product and report the
+    time per replay (CUDA events).  python -m paper_1303_1651_gb300.batched [--count 512] [--replays 5]"""
+    import argparse
+    import json
+    from . import synth
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--count", type=int, default=512)
+    ap.add_argument("--seed", type=int, default=synth.SEED_BATCH)
+    ap.add_argument("--replays", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=2)
+    args = ap.parse_args(argv)
+    A, B, _ = concat(synth.batch_problems(count=args.count, seed=args.seed))
+    dev = torch.device("cuda", 0)
+    dA, dB = binding.DeviceCSR.from_host(A, dev), binding.DeviceCSR.from_host(B, dev)
+    bp = BatchedProduct(dA, dB)
+    for _ in range(args.warmup):
+        bp.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.replays):
+        bp.run()
+    e1.record()
+    torch.cuda.synchronize()
+    bp.check()
+    ms = e0.elapsed_time(e1) / max(args.replays, 1)
+    print(json.dumps({"problems": args.count, "rows": A.rows, "products": bp.info["products"],
+                      "rows_per_class": bp.info["rows_per_class"], "ms_per_replay": ms,
+                      "gflops": 2 * bp.info["products"] / (ms * 1e-3) / 1e9}))
+    bp.close()
+
+
+if __name__ == "__main__":
+    main()
