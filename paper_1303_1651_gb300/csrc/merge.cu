@@ -40,6 +40,11 @@
 // Rows of B need not be sorted: the network orders everything.  Keys hold the
 // column above 5 or 6 index bits, so B may have at most 2^26 - 2 columns; wider
 // matrices use the hash classes.
+//
+// Rows of up to 64 products are split over lanes: two lanes per row in the symbolic
+// and numeric passes (k_merge_pair), four in the fused pass (k_merge_quad below);
+// both give the same sums as one lane per row.  The fused pass places its tiles in
+// groups of four warps (one CTA), one look-back per group.
 #include "internal.h"
 
 namespace spg {
